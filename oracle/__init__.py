@@ -1,0 +1,160 @@
+"""CPU oracle for the two-electron TDA gradient term (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It wraps ``tdgrad_oracle.c`` (plain fp64 C,
+OpenMP) through ctypes.  It shares no code with the CUDA library and the
+product never calls it.
+
+Functions follow the paper's Sec. II.C (Cartesian Gaussians eq. cartG, the
+derivative rule eq. deriv, the centre decomposition eq. deri) and the AO
+gradient's two-electron terms (eq. dE_ao with eq. gamma as (A, B, c) pairs).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tdgrad_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force=False):
+    """Compile the oracle with gcc (OpenMP).  Idempotent."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.or_boys.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
+        lib.or_normalise.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp]
+        basis_args = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _ip, _dp, _dp]
+        lib.or_shell_eri.argtypes = basis_args + [ctypes.c_int] * 4 + [ctypes.c_double, _dp]
+        lib.or_shell_eri_deriv.argtypes = basis_args + [ctypes.c_int] * 4 + [ctypes.c_double, _dp]
+        lib.or_schwarz.argtypes = basis_args + [_dp, _dp]
+        lib.or_grad2e.argtypes = basis_args + [
+            ctypes.c_int, ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, _dp, _dp, _dp,
+            ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]
+        lib.or_grad2e.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+class _Basis:
+    def __init__(self, s):
+        self.natom = int(s["natom"])
+        self.xyz = np.ascontiguousarray(s["xyz"], dtype=np.float64)
+        self.sh_atom = np.ascontiguousarray(s["shell_atom"], dtype=np.int32)
+        self.sh_l = np.ascontiguousarray(s["shell_l"], dtype=np.int32)
+        self.sh_nprim = np.ascontiguousarray(s["shell_nprim"], dtype=np.int32)
+        self.exps = np.ascontiguousarray(s["exps"], dtype=np.float64)
+        self.coefs = np.ascontiguousarray(s["coefs"], dtype=np.float64)
+
+    def args(self):
+        return [self.natom, _d(self.xyz), len(self.sh_l), _i(self.sh_atom), _i(self.sh_l),
+                _i(self.sh_nprim), _d(self.exps), _d(self.coefs)]
+
+
+def boys(mmax, T, branch=0):
+    """[F_0(T) .. F_mmax(T)]; branch 1 = series+downward, 2 = erf+upward."""
+    out = np.zeros(mmax + 1)
+    _load().or_boys(mmax, float(T), branch, _d(out))
+    return out
+
+
+def normalised_coefs(s):
+    b = _Basis(s)
+    out = np.zeros_like(b.exps)
+    _load().or_normalise(len(b.sh_l), _i(b.sh_l), _i(b.sh_nprim), _d(b.exps), _d(b.coefs), _d(out))
+    return out
+
+
+def _nc(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def shell_eri(s, a, b, c, d, omega=0.0):
+    """Contracted (ab|cd) for one shell quartet; omega>0 selects erf(omega r)/r."""
+    bs = _Basis(s)
+    dims = [_nc(int(bs.sh_l[x])) for x in (a, b, c, d)]
+    out = np.zeros(int(np.prod(dims)))
+    _load().or_shell_eri(*bs.args(), a, b, c, d, float(omega), _d(out))
+    return out.reshape(dims)
+
+
+def shell_eri_deriv(s, a, b, c, d, omega=0.0):
+    """d(ab|cd)/dX_i for X = a, b, c, d: array [4, 3, na, nb, nc, nd]."""
+    bs = _Basis(s)
+    dims = [_nc(int(bs.sh_l[x])) for x in (a, b, c, d)]
+    out = np.zeros(12 * int(np.prod(dims)))
+    _load().or_shell_eri_deriv(*bs.args(), a, b, c, d, float(omega), _d(out))
+    return out.reshape([4, 3] + dims)
+
+
+def schwarz(s):
+    """(Q, Q') over all shell pairs, each nshell x nshell."""
+    bs = _Basis(s)
+    n = len(bs.sh_l)
+    Q = np.zeros((n, n))
+    Qd = np.zeros((n, n))
+    _load().or_schwarz(*bs.args(), _d(Q), _d(Qd))
+    return Q, Qd
+
+
+def grad2e(s, pairs=None, mode="canonical", tau=0.0, rank=0, nranks=1, nthreads=0,
+           want_grad=True, want_energy=False, xyz=None):
+    """Two-electron gradient (natom x 3, Ha/bohr) of the pair list.
+
+    Returns (grad, energy, nquartets).  mode "plain" loops over all ordered
+    shell quartets; "canonical" uses the 8-fold symmetry and supports
+    screening (tau) and shards (rank, nranks)."""
+    s2 = dict(s)
+    if xyz is not None:
+        s2["xyz"] = xyz
+    bs = _Basis(s2)
+    pairs = s["pairs"] if pairs is None else pairs
+    npair = len(pairs)
+    mats = [(np.ascontiguousarray(p[0], dtype=np.float64), np.ascontiguousarray(p[1], dtype=np.float64))
+            for p in pairs]
+    Ap = (_dp * max(npair, 1))(*[_d(m[0]) for m in mats])
+    Bp = (_dp * max(npair, 1))(*[_d(m[1]) for m in mats])
+    cJ = np.array([p[2] for p in pairs] + [0.0])
+    cK = np.array([p[3] for p in pairs] + [0.0])
+    cKlr = np.array([p[4] for p in pairs] + [0.0])
+    om = np.array([p[5] for p in pairs] + [0.0])
+    grad = np.zeros((bs.natom, 3))
+    e = ctypes.c_double(0.0)
+    nq = ctypes.c_longlong(0)
+    rc = _load().or_grad2e(*bs.args(), npair, Ap, Bp, _d(cJ), _d(cK), _d(cKlr), _d(om),
+                           0 if mode == "plain" else 1, float(tau), int(rank), int(nranks),
+                           int(nthreads), 1 if want_grad else 0, _d(grad),
+                           ctypes.byref(e) if want_energy else None, ctypes.byref(nq))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return grad, (e.value if want_energy else None), nq.value
