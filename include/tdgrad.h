@@ -1,0 +1,132 @@
+/*
+ * tdgrad — two-electron term of the TDA-TDDFT nuclear gradient on GB300.
+ *
+ * C-ABI of libtdgrad.so.  The library evaluates, for a list of density-matrix
+ * pairs (A, B, c_J, c_K, c_K_lr, omega),
+ *
+ *   g[E,x] = sum_pairs sum_{mu nu lam sig, all ordered}
+ *              [ c_J   d(mu nu|lam sig)/dE_x    A_{mu nu}  B_{lam sig}
+ *              + c_K   d(mu nu|lam sig)/dE_x    A_{mu lam} B_{nu sig}
+ *              + c_K_lr d(mu nu|lam sig)_w/dE_x A_{mu lam} B_{nu sig} ],
+ *
+ * the 4th and 5th terms of the AO-basis excited-state gradient (Sec. II.A,
+ * eq. dE_ao) with the two-particle densities Gamma and Gamma^lr of eq. gamma
+ * written as pairs: Gamma = (R,R; c_J=2, c_K=-alpha, c_K_lr=-beta) +
+ * (P+2P_delta, P; 1/2, -alpha/4, -beta/4).  (|)_w is the erf(omega r)/r
+ * operator of eq. lreri_k; d/dE_x follows eqs. deriv and deri (Sec. II.C).
+ *
+ * Conventions
+ *  - Coordinates in bohr, gradient in hartree/bohr.
+ *  - Cartesian Gaussian shells (eq. cartG) with l <= 2; components in
+ *    lexicographic order (xx, xy, xz, yy, yz, zz).  Contraction coefficients
+ *    multiply normalised primitives, and every component carries the x^l
+ *    normalisation N_k N_c of its shell.
+ *  - Density matrices are nbf x nbf, row-major, in that AO order; they need
+ *    not be symmetric.
+ *  - All pairs with c_K_lr != 0 and omega > 0 must share one omega
+ *    (TG_EUNSUPPORTED otherwise).  omega <= 0 or c_K_lr = 0 drops the lr term;
+ *    omega = +inf makes the lr operator equal to 1/r.
+ *  - Screening (Sec. II.E, density-multiplied Schwarz bound): a canonical
+ *    shell quartet is skipped iff
+ *      8 * npair * max(Q'_ab Q_cd, Q_ab Q'_cd) * M_q^2 < screen_tol,
+ *    with Q_ab = max_{mu nu} sum_{kl} |c_k c_l| sqrt((k_mu l_nu|k_mu l_nu)),
+ *    Q'_ab the same with the primitive mu or nu replaced by its derivative
+ *    function (maximised over centre and direction), and M_q the largest of
+ *    M(x,y) = max_p sqrt(|c_J|+|c_K|+|c_K_lr|) max(|A_p|,|B_p|) over the shell
+ *    blocks ab, cd, ac, ad, bc, bd (both orientations).  screen_tol = 0 keeps
+ *    every quartet.
+ *  - Shards (rank, nranks): a canonical quartet belongs to a shard iff
+ *    max(key(a,b), key(c,d)) mod nranks == rank, key(x,y) = X(X+1)/2 + Y,
+ *    X = max(x,y), Y = min(x,y) over shell indices.  Partial gradients of all
+ *    shards sum to the full one.
+ *
+ * Ownership: the caller owns every pointer it passes.  The library copies
+ * what it needs during a call and keeps no caller pointer after return; only
+ * the opaque handles persist, and they own their device memory.
+ * Threading: a handle may be used by one host thread at a time.
+ * Errors: every call returns TG_OK (0) or a negative status; on error the
+ * output arrays are left untouched.  tg_strerror() names a status.
+ */
+#ifndef TDGRAD_H
+#define TDGRAD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TG_OK 0
+#define TG_EINVAL (-1)        /* bad argument (null, size, exponent <= 0 ...) */
+#define TG_EUNSUPPORTED (-2)  /* l > 2, more than one lr omega, too many pairs */
+#define TG_ENOMEM (-3)        /* device or host allocation failed */
+#define TG_ECUDA (-4)         /* a CUDA runtime call failed */
+#define TG_ETIMEOUT (-5)      /* a bounded device wait expired */
+#define TG_EROUTER (-6)       /* router missing, malformed or incompatible */
+
+#define TG_FP64 0             /* every primitive quartet in fp64 */
+#define TG_MIXED_BOUND 1      /* fp32/fp64 routing by the rigorous bound */
+#define TG_MIXED_LEARNED 2    /* fp32/fp64 routing by the learned router */
+
+#define TG_MAX_PAIRS 8
+
+typedef struct tg_basis tg_basis;    /* opaque: basis + geometry, device copies */
+typedef struct tg_router tg_router;  /* opaque: block router MLP weights */
+
+/* One density pair.  A and B are nbf*nbf doubles, row-major; host pointers
+ * unless tg_options.device_ptrs is set, then device pointers. */
+typedef struct {
+    const double *A, *B;
+    double c_J, c_K, c_K_lr, omega;
+} tg_pair;
+
+typedef struct {
+    double screen_tol;      /* density-multiplied Schwarz threshold; default 1e-10 (Sec. II.E) */
+    int precision;          /* TG_FP64 (default), TG_MIXED_BOUND, TG_MIXED_LEARNED */
+    const tg_router *router;/* required for TG_MIXED_LEARNED */
+    double mixed_tol;       /* target max |dg| of the fp32 route, default 1e-6 Ha/bohr */
+    int device_ptrs;        /* 1: A, B and grad are device pointers */
+    void *stream;           /* cudaStream_t; NULL = legacy default stream */
+    int rank, nranks;       /* shard; default 0 / 1 */
+    int timing;             /* 1: time every class kernel with CUDA events (tg_stats.class_ms) */
+    int reserved[7];
+} tg_options;
+
+typedef struct {
+    double seconds;               /* wall time of the call (host clock) */
+    long long quartets;           /* canonical shell quartets evaluated */
+    long long prim_quartets;      /* primitive quartets evaluated */
+    long long fp32_quartets;      /* quartets routed to fp32 */
+    long long pairs;              /* shell pairs kept after pair screening */
+    long long tiles;              /* quartet tiles launched */
+    int launches;                 /* CUDA kernels launched by the call */
+    int grid;                     /* CTAs of each persistent class launch */
+    double class_ms[21];          /* per angular class: kernel time (only with timing = 1) */
+    long long class_quartets[21];
+    long long class_prim_quartets[21];
+} tg_stats;
+
+/* Fill o with the defaults listed above. */
+void tg_options_default(tg_options *o);
+
+/* Create a basis handle.  xyz_bohr: natom*3; per shell: atom index, l (0..2),
+ * primitive count (1..16); exps/coefs: concatenated primitives in shell
+ * order, exps > 0.  Uploads the basis and computes the Schwarz factors Q, Q'
+ * on the current CUDA device (eq. cartG normalisation, Sec. II.C). */
+int tg_basis_create(int natom, const double *xyz_bohr, int nshell, const int *shell_atom,
+                    const int *shell_l, const int *shell_nprim, const double *exps,
+                    const double *coefs, tg_basis **out);
+int tg_basis_nbf(const tg_basis *b);
+int tg_basis_natom(const tg_basis *b);
+void tg_basis_destroy(tg_basis *b);
+
+/* The two-electron gradient (see the top of this file).  grad: natom*3
+ * doubles, overwritten (host unless device_ptrs).  stats may be NULL.
+ * npair in 1..TG_MAX_PAIRS.  opt may be NULL (defaults). */
+int tg_grad2e(const tg_basis *b, int npair, const tg_pair *pairs, const tg_options *opt,
+              double *grad, tg_stats *stats);
+
+const char *tg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

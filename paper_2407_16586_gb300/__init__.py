@@ -1,0 +1,217 @@
+"""tdgrad: the two-electron term of the TDA-TDDFT nuclear gradient on GB300.
+
+Thin ctypes binding of libtdgrad.so (C-ABI in include/tdgrad.h).  It only
+marshals arguments: every step of the gradient runs in the library's CUDA
+kernels.  There is no CPU fallback; a missing library raises.
+
+The functions keep the C names (tg_basis_create, tg_grad2e, ...).  ``Basis``
+and ``grad2e`` are conveniences over them for dict-shaped systems such as
+those returned by ``paper_2407_16586_gb300.synth``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdgrad.so")
+
+TG_OK = 0
+TG_EINVAL = -1
+TG_EUNSUPPORTED = -2
+TG_ENOMEM = -3
+TG_ECUDA = -4
+TG_ETIMEOUT = -5
+TG_EROUTER = -6
+
+TG_FP64 = 0
+TG_MIXED_BOUND = 1
+TG_MIXED_LEARNED = 2
+TG_MAX_PAIRS = 8
+
+EXPORTS = ("tg_options_default", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
+           "tg_grad2e", "tg_strerror")
+
+
+class tg_pair(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("c_J", ctypes.c_double),
+                ("c_K", ctypes.c_double), ("c_K_lr", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class tg_options(ctypes.Structure):
+    _fields_ = [("screen_tol", ctypes.c_double), ("precision", ctypes.c_int), ("router", ctypes.c_void_p),
+                ("mixed_tol", ctypes.c_double), ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("rank", ctypes.c_int), ("nranks", ctypes.c_int), ("timing", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class tg_stats(ctypes.Structure):
+    _fields_ = [("seconds", ctypes.c_double), ("quartets", ctypes.c_longlong), ("prim_quartets", ctypes.c_longlong),
+                ("fp32_quartets", ctypes.c_longlong), ("pairs", ctypes.c_longlong), ("tiles", ctypes.c_longlong),
+                ("launches", ctypes.c_int), ("grid", ctypes.c_int), ("class_ms", ctypes.c_double * 21),
+                ("class_quartets", ctypes.c_longlong * 21), ("class_prim_quartets", ctypes.c_longlong * 21)]
+
+    def as_dict(self):
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if hasattr(v, "_length_") else v
+        return out
+
+
+class TGError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (where, tg_strerror(status), status))
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libtdgrad.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtdgrad.so is not built (run paper_2407_16586_gb300.build.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+        L.tg_options_default.argtypes = [ctypes.POINTER(tg_options)]
+        L.tg_options_default.restype = None
+        L.tg_basis_create.argtypes = [ctypes.c_int, dp, ctypes.c_int, ip, ip, ip, dp, dp, ctypes.POINTER(vp)]
+        L.tg_basis_create.restype = ctypes.c_int
+        L.tg_basis_nbf.argtypes = [vp]
+        L.tg_basis_nbf.restype = ctypes.c_int
+        L.tg_basis_natom.argtypes = [vp]
+        L.tg_basis_natom.restype = ctypes.c_int
+        L.tg_basis_destroy.argtypes = [vp]
+        L.tg_basis_destroy.restype = None
+        L.tg_grad2e.argtypes = [vp, ctypes.c_int, ctypes.POINTER(tg_pair), ctypes.POINTER(tg_options), vp,
+                                ctypes.POINTER(tg_stats)]
+        L.tg_grad2e.restype = ctypes.c_int
+        L.tg_strerror.argtypes = [ctypes.c_int]
+        L.tg_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def tg_strerror(status):
+    return lib().tg_strerror(int(status)).decode()
+
+
+def tg_options_default():
+    o = tg_options()
+    lib().tg_options_default(ctypes.byref(o))
+    return o
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def tg_basis_create(natom, xyz, nshell, shell_atom, shell_l, shell_nprim, exps, coefs):
+    xyz, shell_atom, shell_l = _c(xyz, np.float64), _c(shell_atom, np.int32), _c(shell_l, np.int32)
+    shell_nprim, exps, coefs = _c(shell_nprim, np.int32), _c(exps, np.float64), _c(coefs, np.float64)
+    h = ctypes.c_void_p()
+    dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    rc = lib().tg_basis_create(int(natom), xyz.ctypes.data_as(dp), int(nshell), shell_atom.ctypes.data_as(ip),
+                               shell_l.ctypes.data_as(ip), shell_nprim.ctypes.data_as(ip), exps.ctypes.data_as(dp),
+                               coefs.ctypes.data_as(dp), ctypes.byref(h))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_basis_create")
+    return h
+
+
+def tg_basis_nbf(h):
+    return lib().tg_basis_nbf(h)
+
+
+def tg_basis_natom(h):
+    return lib().tg_basis_natom(h)
+
+
+def tg_basis_destroy(h):
+    lib().tg_basis_destroy(h)
+
+
+def tg_grad2e(h, pairs, options=None, grad_ptr=None, natom=None):
+    """pairs: list of (A_ptr, B_ptr, c_J, c_K, c_K_lr, omega) with raw pointers
+    (host or device per options.device_ptrs).  grad_ptr: raw output pointer;
+    returns (status, tg_stats)."""
+    arr = (tg_pair * len(pairs))()
+    for i, (a, b, cj, ck, cl, om) in enumerate(pairs):
+        arr[i] = tg_pair(a, b, cj, ck, cl, om)
+    st = tg_stats()
+    opt = options if options is not None else tg_options_default()
+    rc = lib().tg_grad2e(h, len(pairs), arr, ctypes.byref(opt), grad_ptr, ctypes.byref(st))
+    return rc, st
+
+
+class Basis:
+    """Owns a tg_basis handle built from a dict-shaped system."""
+
+    def __init__(self, system):
+        self.natom = int(system["natom"])
+        self.nshell = len(system["shell_l"])
+        self.h = tg_basis_create(self.natom, system["xyz"], self.nshell, system["shell_atom"], system["shell_l"],
+                                 system["shell_nprim"], system["exps"], system["coefs"])
+        self.nbf = tg_basis_nbf(self.h)
+
+    def close(self):
+        if self.h is not None:
+            tg_basis_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
+               timing=False):
+        """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
+        torch CUDA tensors (then the densities and ``out`` stay on the device)."""
+        opt = tg_options_default()
+        opt.screen_tol = float(screen_tol)
+        opt.precision = int(precision)
+        opt.rank, opt.nranks = int(rank), int(nranks)
+        opt.timing = 1 if timing else 0
+        dev = hasattr(pairs[0][0], "is_cuda") and pairs[0][0].is_cuda
+        keep = []
+        plist = []
+        for (a, b, cj, ck, cl, om) in pairs:
+            if dev:
+                a, b = a.contiguous(), b.contiguous()
+                keep += [a, b]
+                plist.append((a.data_ptr(), b.data_ptr(), float(cj), float(ck), float(cl), float(om)))
+            else:
+                a, b = _c(a, np.float64), _c(b, np.float64)
+                keep += [a, b]
+                plist.append((a.ctypes.data, b.ctypes.data, float(cj), float(ck), float(cl), float(om)))
+        if dev:
+            import torch
+            opt.device_ptrs = 1
+            opt.stream = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+            g = out if out is not None else torch.empty((self.natom, 3), dtype=torch.float64, device=pairs[0][0].device)
+            rc, st = tg_grad2e(self.h, plist, opt, ctypes.c_void_p(g.data_ptr()))
+        else:
+            g = out if out is not None else np.zeros((self.natom, 3))
+            if stream is not None:
+                opt.stream = ctypes.c_void_p(stream)
+            rc, st = tg_grad2e(self.h, plist, opt, ctypes.c_void_p(g.ctypes.data))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_grad2e")
+        return g, st.as_dict()
+
+
+def grad2e(system, pairs=None, **kw):
+    """One-shot gradient of a dict-shaped system (builds and frees a Basis)."""
+    b = Basis(system)
+    try:
+        return b.grad2e(system["pairs"] if pairs is None else pairs, **kw)
+    finally:
+        b.close()

@@ -1,0 +1,875 @@
+// Derivative-ERI class kernels fused with the J/K/K_lr density contraction
+// and the per-atom reduction.  One template instance per angular class
+// (la lb|lc ld) with la >= lb, lc >= ld and bra pair class >= ket pair class:
+// the 21 non-redundant classes for l <= 2 (Sec. II.C).
+//
+// Per contracted shell quartet (one thread), per primitive quartet, with the
+// McMurchie-Davidson expansion
+//   (ab|cd) = sum_{h1,h2} E^{ab}_{h1} E^{cd}_{h2} (-1)^{|h2|} R_{h1+h2},
+// the derivative of eq. deri is taken as
+//   d/dA  : E^{ab} -> DA = 2 zeta_a E^{a+1,b} - a_x E^{a-1,b} (eq. deriv)
+//   d/dC  : E^{cd} -> DC likewise
+//   d/dA + d/dB = d/dP : R_{h} -> R_{h+1_x}
+// and d/dB, d/dD follow from translational invariance (eq. ti).  The density
+// contraction (eq. eriupdate summed over a canonical quartet's 8 images) is
+// folded in at the half-transformed level:
+//   y^{ab}_{h1} = sum_s sum_{h2} [sum_{cd} Gamma_s^{ab,cd} E^{cd}_{h2}] (-1)^{|h2|} R^s_{h1+h2}
+//   z^{cd}_{h2} = sum_s sum_{h1} [sum_{ab} Gamma_s^{ab,cd} E^{ab}_{h1}] R^s_{h1+h2}
+// with s over the 1/r and erf(w r)/r operators (Gamma_full, Gamma_lr), so
+// each gradient component is a short dot product with y or z.
+#pragma once
+#include "tg_internal.cuh"
+
+namespace tg {
+
+// loop over the Cartesian component pairs of two shells, unrolled (exponents
+// are compile-time constants) or not
+template <int LX, int LY, bool UNR, typename Fn>
+__device__ __forceinline__ void for_pairs(Fn &&fn)
+{
+    if constexpr (UNR) {
+#pragma unroll
+        for (int ax = LX; ax >= 0; --ax)
+#pragma unroll
+            for (int ay = LX - ax; ay >= 0; --ay)
+#pragma unroll
+                for (int bx = LY; bx >= 0; --bx)
+#pragma unroll
+                    for (int by = LY - bx; by >= 0; --by)
+                        fn(ax, ay, LX - ax - ay, bx, by, LY - bx - by);
+    } else {
+#pragma unroll 1
+        for (int ax = LX; ax >= 0; --ax)
+#pragma unroll 1
+            for (int ay = LX - ax; ay >= 0; --ay)
+#pragma unroll 1
+                for (int bx = LY; bx >= 0; --bx)
+#pragma unroll 1
+                    for (int by = LY - bx; by >= 0; --by)
+                        fn(ax, ay, LX - ax - ay, bx, by, LY - bx - by);
+    }
+}
+
+// Gamma_full and Gamma_lr of the canonical quartet (a b|c d): the sum over
+// the 8 permutation images of the ordered density products, times `scale`
+// (1/|stabiliser|), summed over the pairs.
+template <int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void build_gamma(const DensArgs &den, int fa, int fb, int fc, int fd, double scale,
+                                            double *gam, double *gaml)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int NCD = NC * ND;
+    const int nbf = den.nbf;
+    for (int k = 0; k < NA * NB * NCD; ++k) {
+        gam[k] = 0.0;
+        gaml[k] = 0.0;
+    }
+    for (int p = 0; p < den.npair; ++p) {
+        const double *__restrict__ A = den.A[p];
+        const double *__restrict__ B = den.B[p];
+        const double *__restrict__ S = den.S[p];
+        const double *__restrict__ T = den.T[p];
+        const double cj = den.cJ[p] * scale, ck = den.cK[p] * scale, cl = den.cKlr[p] * scale;
+        const bool doj = cj != 0.0, dok = (ck != 0.0) || (cl != 0.0);
+        if (!doj && !dok) continue;
+#pragma unroll 1
+        for (int ma = 0; ma < NA; ++ma)
+#pragma unroll 1
+            for (int mb = 0; mb < NB; ++mb) {
+                const size_t m = fa + ma, n = fb + mb;
+                const double smn = S[m * nbf + n], tmn = T[m * nbf + n];
+#pragma unroll 1
+                for (int mc = 0; mc < NC; ++mc)
+                    for (int md = 0; md < ND; ++md) {
+                        const size_t l = fc + mc, s = fd + md;
+                        const int k = (ma * NB + mb) * NCD + mc * ND + md;
+                        if (doj) gam[k] += cj * (smn * T[l * nbf + s] + S[l * nbf + s] * tmn);
+                        if (dok) {
+                            double kk = A[m * nbf + l] * B[n * nbf + s] + A[n * nbf + l] * B[m * nbf + s] +
+                                        A[m * nbf + s] * B[n * nbf + l] + A[n * nbf + s] * B[m * nbf + l] +
+                                        A[l * nbf + m] * B[s * nbf + n] + A[s * nbf + m] * B[l * nbf + n] +
+                                        A[l * nbf + n] * B[s * nbf + m] + A[s * nbf + n] * B[l * nbf + m];
+                            gam[k] += ck * kk;
+                            gaml[k] += cl * kk;
+                        }
+                    }
+            }
+    }
+}
+
+// One canonical shell quartet in fp64.  g[12] receives d/dA, d/dB, d/dC, d/dD
+// (x, y, z each) of sum Gamma (ab|cd) over both operators.
+template <int LA, int LB, int LC, int LD>
+__device__ void quartet_fp64(const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp, int sa, int sb, int sc,
+                             int sd, int pb0, int nbp, int pk0, int nkp, double scale, const double *boys,
+                             double (&g)[12])
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int NAB = NA * NB, NCD = NC * ND;
+    constexpr int L1 = LA + LB, L2 = LC + LD, L = L1 + L2;
+    constexpr int NH1 = nherm(L1), NH1P = nherm(L1 + 1), NH2 = nherm(L2), NH2P = nherm(L2 + 1);
+    constexpr int NR = nherm(L + 1);
+    constexpr bool UAB = NAB * NH1P * NH2 <= 64;
+    constexpr bool UCD = NCD * NH2P * NH1 <= 64;
+
+    double gam[NAB * NCD], gaml[NAB * NCD];
+    build_gamma<LA, LB, LC, LD>(den, geo.sh_bf[sa], geo.sh_bf[sb], geo.sh_bf[sc], geo.sh_bf[sd], scale, gam, gaml);
+    const bool lr = den.use_lr;
+    const double om2 = den.omega * den.omega;
+    const bool ominf = isinf(den.omega);
+
+    const double *xa = geo.xyz + 3 * geo.sh_atom[sa], *xb = geo.xyz + 3 * geo.sh_atom[sb];
+    const double *xc = geo.xyz + 3 * geo.sh_atom[sc], *xd = geo.xyz + 3 * geo.sh_atom[sd];
+    const double Ax = xa[0], Ay = xa[1], Az = xa[2], Bx = xb[0], By = xb[1], Bz = xb[2];
+    const double Cx = xc[0], Cy = xc[1], Cz = xc[2], Dx = xd[0], Dy = xd[1], Dz = xd[2];
+
+    double gA[3] = {0, 0, 0}, gC[3] = {0, 0, 0}, gT[3] = {0, 0, 0};
+
+    for (int ib = 0; ib < nbp; ++ib) {
+        const int ip = pb0 + ib;
+        const double p = pp.p[ip], Px = pp.Px[ip], Py = pp.Py[ip], Pz = pp.Pz[ip], Kab = pp.K[ip];
+        const double za2 = 2.0 * pp.za[ip];
+        const double oo2p = 0.5 / p;
+        double Ebx[LA + 2][LB + 1][L1 + 2], Eby[LA + 2][LB + 1][L1 + 2], Ebz[LA + 2][LB + 1][L1 + 2];
+        etab<LA + 1, LB>(Ebx, Px - Ax, Px - Bx, oo2p);
+        etab<LA + 1, LB>(Eby, Py - Ay, Py - By, oo2p);
+        etab<LA + 1, LB>(Ebz, Pz - Az, Pz - Bz, oo2p);
+
+        // F_s[cd][h1] = sum_ab Gamma_s[ab][cd] E^{ab}_{h1}
+        double Fa[NCD][NH1], Fl[NCD][NH1];
+#pragma unroll
+        for (int k = 0; k < NCD; ++k)
+#pragma unroll
+            for (int h = 0; h < NH1; ++h) {
+                Fa[k][h] = 0.0;
+                Fl[k][h] = 0.0;
+            }
+        {
+            int ab = 0;
+            for_pairs<LA, LB, UAB>([&](int ax, int ay, int az, int bx, int by, int bz) {
+                for (int t = 0; t <= ax + bx; ++t)
+                    for (int u = 0; u <= ay + by; ++u)
+                        for (int v = 0; v <= az + bz; ++v) {
+                            const double e = Ebx[ax][bx][t] * Eby[ay][by][u] * Ebz[az][bz][v];
+                            const int h = hidx(t, u, v);
+#pragma unroll
+                            for (int k = 0; k < NCD; ++k) {
+                                Fa[k][h] += gam[ab * NCD + k] * e;
+                                if (lr) Fl[k][h] += gaml[ab * NCD + k] * e;
+                            }
+                        }
+                ++ab;
+            });
+        }
+
+        for (int jk = 0; jk < nkp; ++jk) {
+            const int kp = pk0 + jk;
+            const double q = pp.p[kp], Qx = pp.Px[kp], Qy = pp.Py[kp], Qz = pp.Pz[kp], Kcd = pp.K[kp];
+            const double zc2 = 2.0 * pp.za[kp];
+            const double oo2q = 0.5 / q;
+            double Ekx[LC + 2][LD + 1][L2 + 2], Eky[LC + 2][LD + 1][L2 + 2], Ekz[LC + 2][LD + 1][L2 + 2];
+            etab<LC + 1, LD>(Ekx, Qx - Cx, Qx - Dx, oo2q);
+            etab<LC + 1, LD>(Eky, Qy - Cy, Qy - Dy, oo2q);
+            etab<LC + 1, LD>(Ekz, Qz - Cz, Qz - Dz, oo2q);
+
+            // R tensors of both operators, prefactor and contraction coefficients included
+            const double pq = p + q;
+            const double rho = p * q / pq;
+            const double X = Px - Qx, Y = Py - Qy, Z = Pz - Qz;
+            const double T = rho * (X * X + Y * Y + Z * Z);
+            const double pref = 34.986836655249725 / (p * q * sqrt(pq)) * Kab * Kcd;  // 2 pi^(5/2)
+            double R[NR], Rl[NR];
+            {
+                double Fm[L + 2], base[L + 2];
+                boys_fp64<L + 1>(T, Fm, boys);
+                double f = pref, m2r = -2.0 * rho;
+#pragma unroll
+                for (int n = 0; n <= L + 1; ++n) {
+                    base[n] = f * Fm[n];
+                    f *= m2r;
+                }
+                hermite_R<L + 1>(R, base, X, Y, Z);
+                if (lr) {
+                    const double th2 = ominf ? 1.0 : om2 / (om2 + rho);
+                    boys_fp64<L + 1>(T * th2, Fm, boys);
+                    double fl = pref * sqrt(th2), m2rl = -2.0 * rho * th2;
+#pragma unroll
+                    for (int n = 0; n <= L + 1; ++n) {
+                        base[n] = fl * Fm[n];
+                        fl *= m2rl;
+                    }
+                    hermite_R<L + 1>(Rl, base, X, Y, Z);
+                }
+            }
+
+            // ket Hermite products E^{cd}_{h2}
+            double E3k[NCD][NH2];
+            {
+                int cd = 0;
+                for_pairs<LC, LD, true>([&](int cx, int cy, int cz, int dx, int dy, int dz) {
+#pragma unroll
+                    for (int h = 0; h < NH2; ++h) E3k[cd][h] = 0.0;
+#pragma unroll
+                    for (int t = 0; t <= cx + dx; ++t)
+#pragma unroll
+                        for (int u = 0; u <= cy + dy; ++u)
+#pragma unroll
+                            for (int v = 0; v <= cz + dz; ++v)
+                                E3k[cd][hidx(t, u, v)] = Ekx[cx][dx][t] * Eky[cy][dy][u] * Ekz[cz][dz][v];
+                    ++cd;
+                });
+            }
+
+            // ---- bra side: y^{ab}, then d/dA and d/dP
+            {
+                int ab = 0;
+                for_pairs<LA, LB, UAB>([&](int ax, int ay, int az, int bx, int by, int bz) {
+                    double gr[NH2], grl[NH2];
+#pragma unroll 1
+                    for (int h = 0; h < NH2; ++h) {
+                        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+                        for (int k = 0; k < NCD; ++k) {
+                            s0 += gam[ab * NCD + k] * E3k[k][h];
+                            if (lr) s1 += gaml[ab * NCD + k] * E3k[k][h];
+                        }
+                        gr[h] = s0;
+                        grl[h] = s1;
+                    }
+                    double y[NH1P];
+#pragma unroll
+                    for (int h = 0; h < NH1P; ++h) y[h] = 0.0;
+#pragma unroll 1
+                    for (int t2 = 0; t2 <= L2; ++t2)
+#pragma unroll 1
+                        for (int u2 = 0; u2 <= L2 - t2; ++u2)
+#pragma unroll 1
+                            for (int v2 = 0; v2 <= L2 - t2 - u2; ++v2) {
+                                const int h2 = hidx(t2, u2, v2);
+                                const double sg = ((t2 + u2 + v2) & 1) ? -1.0 : 1.0;
+                                const double c0 = sg * gr[h2], c1 = sg * grl[h2];
+#pragma unroll
+                                for (int t1 = 0; t1 <= L1 + 1; ++t1)
+#pragma unroll
+                                    for (int u1 = 0; u1 <= L1 + 1 - t1; ++u1)
+#pragma unroll
+                                        for (int v1 = 0; v1 <= L1 + 1 - t1 - u1; ++v1) {
+                                            const int hr = hidx(t1 + t2, u1 + u2, v1 + v2);
+                                            double acc = y[hidx(t1, u1, v1)] + c0 * R[hr];
+                                            if (lr) acc += c1 * Rl[hr];
+                                            y[hidx(t1, u1, v1)] = acc;
+                                        }
+                            }
+                    // d/dA and d/dP, factorised over t, u, v with exact ranges
+                    const int nx = ax + bx, ny = ay + by, nz = az + bz;
+                    double sz[L1 + 2][L1 + 2];  // sz[t][u] = sum_v E_z(v) y[t,u,v]
+                    for (int t = 0; t <= nx + 1; ++t)
+                        for (int u = 0; u <= ny + 1 && t + u <= L1 + 1; ++u) {
+                            double acc = 0.0;
+                            for (int v = 0; v <= nz && t + u + v <= L1 + 1; ++v) acc += Ebz[az][bz][v] * y[hidx(t, u, v)];
+                            sz[t][u] = acc;
+                        }
+                    double ax_ = 0.0, ay_ = 0.0, az_ = 0.0, tx = 0.0, ty = 0.0, tz = 0.0;
+                    for (int t = 0; t <= nx + 1; ++t) {
+                        const double dxt = za2 * Ebx[ax + 1][bx][t] - (ax > 0 ? ax * Ebx[ax - 1][bx][t] : 0.0);
+                        double s = 0.0;
+                        for (int u = 0; u <= ny; ++u) s += Eby[ay][by][u] * sz[t][u];
+                        ax_ += dxt * s;
+                    }
+                    for (int t = 0; t <= nx; ++t) {
+                        const double ext = Ebx[ax][bx][t];
+                        double sy = 0.0, sx1 = 0.0, sy1 = 0.0, szd = 0.0, sz1 = 0.0;
+                        for (int u = 0; u <= ny + 1; ++u) {
+                            const double dyu = za2 * Eby[ay + 1][by][u] - (ay > 0 ? ay * Eby[ay - 1][by][u] : 0.0);
+                            sy += dyu * sz[t][u];
+                        }
+                        for (int u = 0; u <= ny; ++u) {
+                            const double eyu = Eby[ay][by][u];
+                            sx1 += eyu * sz[t + 1][u];
+                            sy1 += eyu * sz[t][u + 1];
+                            double a1 = 0.0, a2 = 0.0;
+                            for (int v = 0; v <= nz + 1; ++v) {
+                                const double dzv = za2 * Ebz[az + 1][bz][v] - (az > 0 ? az * Ebz[az - 1][bz][v] : 0.0);
+                                a1 += dzv * y[hidx(t, u, v)];
+                            }
+                            for (int v = 0; v <= nz; ++v) a2 += Ebz[az][bz][v] * y[hidx(t, u, v + 1)];
+                            szd += eyu * a1;
+                            sz1 += eyu * a2;
+                        }
+                        ay_ += ext * sy;
+                        az_ += ext * szd;
+                        tx += ext * sx1;
+                        ty += ext * sy1;
+                        tz += ext * sz1;
+                    }
+                    gA[0] += ax_;
+                    gA[1] += ay_;
+                    gA[2] += az_;
+                    gT[0] += tx;
+                    gT[1] += ty;
+                    gT[2] += tz;
+                    ++ab;
+                });
+            }
+
+            // ---- ket side: z^{cd}, then d/dC
+            {
+                int cd = 0;
+                for_pairs<LC, LD, UCD>([&](int cx, int cy, int cz, int dx, int dy, int dz) {
+                    double z[NH2P];
+#pragma unroll
+                    for (int h = 0; h < NH2P; ++h) z[h] = 0.0;
+#pragma unroll 1
+                    for (int t1 = 0; t1 <= L1; ++t1)
+#pragma unroll 1
+                        for (int u1 = 0; u1 <= L1 - t1; ++u1)
+#pragma unroll 1
+                            for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
+                                const int h1 = hidx(t1, u1, v1);
+                                const double f0 = Fa[cd][h1], f1 = Fl[cd][h1];
+#pragma unroll
+                                for (int t2 = 0; t2 <= L2 + 1; ++t2)
+#pragma unroll
+                                    for (int u2 = 0; u2 <= L2 + 1 - t2; ++u2)
+#pragma unroll
+                                        for (int v2 = 0; v2 <= L2 + 1 - t2 - u2; ++v2) {
+                                            const int hr = hidx(t1 + t2, u1 + u2, v1 + v2);
+                                            double acc = z[hidx(t2, u2, v2)] + f0 * R[hr];
+                                            if (lr) acc += f1 * Rl[hr];
+                                            z[hidx(t2, u2, v2)] = acc;
+                                        }
+                            }
+                    // d/dC, factorised; the ket sign (-1)^{t+u+v} is folded into z
+                    const int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+#pragma unroll
+                    for (int t2 = 0; t2 <= L2 + 1; ++t2)
+#pragma unroll
+                        for (int u2 = 0; u2 <= L2 + 1 - t2; ++u2)
+#pragma unroll
+                            for (int v2 = 0; v2 <= L2 + 1 - t2 - u2; ++v2)
+                                if ((t2 + u2 + v2) & 1) z[hidx(t2, u2, v2)] = -z[hidx(t2, u2, v2)];
+                    double sz[L2 + 2][L2 + 2];
+                    for (int t = 0; t <= nx + 1; ++t)
+                        for (int u = 0; u <= ny + 1 && t + u <= L2 + 1; ++u) {
+                            double acc = 0.0;
+                            for (int v = 0; v <= nz && t + u + v <= L2 + 1; ++v) acc += Ekz[cz][dz][v] * z[hidx(t, u, v)];
+                            sz[t][u] = acc;
+                        }
+                    double cx_ = 0.0, cy_ = 0.0, cz_ = 0.0;
+                    for (int t = 0; t <= nx + 1; ++t) {
+                        const double dxt = zc2 * Ekx[cx + 1][dx][t] - (cx > 0 ? cx * Ekx[cx - 1][dx][t] : 0.0);
+                        double s = 0.0;
+                        for (int u = 0; u <= ny; ++u) s += Eky[cy][dy][u] * sz[t][u];
+                        cx_ += dxt * s;
+                    }
+                    for (int t = 0; t <= nx; ++t) {
+                        const double ext = Ekx[cx][dx][t];
+                        double sy = 0.0, szd = 0.0;
+                        for (int u = 0; u <= ny + 1; ++u) {
+                            const double dyu = zc2 * Eky[cy + 1][dy][u] - (cy > 0 ? cy * Eky[cy - 1][dy][u] : 0.0);
+                            sy += dyu * sz[t][u];
+                        }
+                        for (int u = 0; u <= ny; ++u) {
+                            double a1 = 0.0;
+                            for (int v = 0; v <= nz + 1; ++v) {
+                                const double dzv = zc2 * Ekz[cz + 1][dz][v] - (cz > 0 ? cz * Ekz[cz - 1][dz][v] : 0.0);
+                                a1 += dzv * z[hidx(t, u, v)];
+                            }
+                            szd += Eky[cy][dy][u] * a1;
+                        }
+                        cy_ += ext * sy;
+                        cz_ += ext * szd;
+                    }
+                    gC[0] += cx_;
+                    gC[1] += cy_;
+                    gC[2] += cz_;
+                    ++cd;
+                });
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g[i] = gA[i];
+        g[3 + i] = gT[i] - gA[i];
+        g[6 + i] = gC[i];
+        g[9 + i] = -gT[i] - gC[i];
+    }
+}
+
+// fp32 Boys function F_m(T), m = 0..M: same Taylor table (read in fp64 and
+// rounded) and downward recursion in fp32 for T >= 1; for T < 1 the fp64
+// routine is used.  Relative accuracy ~1e-7.
+template <int M>
+__device__ __forceinline__ void boys_mixed(double Td, float (&F)[M + 1], const double *__restrict__ tab)
+{
+    if (Td < 1.0) {
+        double Fd[M + 1];
+        boys_fp64<M>(Td, Fd, tab);
+#pragma unroll
+        for (int m = 0; m <= M; ++m) F[m] = (float)Fd[m];
+        return;
+    }
+    const float T = (float)Td;
+    if (Td < BOYS_TMAX) {
+        const int i = __float2int_rn(T * (float)(1.0 / BOYS_H));
+        const float d = (float)(i * BOYS_H - Td);
+        const double *row = tab + i * (BOYS_M + 1) + M;
+        float acc = (float)row[BOYS_TAYLOR];
+#pragma unroll
+        for (int k = BOYS_TAYLOR - 1; k >= 0; --k) acc = (float)row[k] + acc * d * (1.0f / (k + 1));
+        F[M] = acc;
+        const float et = __expf(-T);
+        const float t2 = 2.0f * T;
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m) F[m] = (t2 * F[m + 1] + et) * (1.0f / (2 * m + 1));
+    } else {
+        const float it = 1.0f / T;
+        F[0] = 0.88622692545275801365f * sqrtf(it);
+        const float et = __expf(-T);
+        const float h = 0.5f * it;
+#pragma unroll
+        for (int m = 0; m < M; ++m) F[m + 1] = ((2 * m + 1) * F[m] - et) * h;
+    }
+}
+
+// One canonical shell quartet with fp32 primitive arithmetic.  Same algebra
+// as quartet_fp64, in the scaled Hermite basis R'_h = R_h / s^{|h|},
+// s = sqrt(2 rho): R'^{(n)}_{000} = pref (-1)^n F_n and the recursion runs
+// with X s, so every intermediate stays within fp32 range for any exponent.
+// The factors s^{|h|} are moved onto the short Hermite vectors (G rows,
+// F rows, y, z).  Each bra primitive's contribution is added in fp64.
+template <int LA, int LB, int LC, int LD>
+__device__ void quartet_fp32(const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp, int sa, int sb, int sc,
+                             int sd, int pb0, int nbp, int pk0, int nkp, double scale, const double *boys,
+                             double (&g)[12])
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int NAB = NA * NB, NCD = NC * ND;
+    constexpr int L1 = LA + LB, L2 = LC + LD, L = L1 + L2;
+    constexpr int NH1 = nherm(L1), NH1P = nherm(L1 + 1), NH2 = nherm(L2), NH2P = nherm(L2 + 1);
+    constexpr int NR = nherm(L + 1);
+    constexpr bool UAB = NAB * NH1P * NH2 <= 64;
+    constexpr bool UCD = NCD * NH2P * NH1 <= 64;
+
+    float gam[NAB * NCD], gaml[NAB * NCD];
+    {
+        double gd[NAB * NCD], gdl[NAB * NCD];
+        build_gamma<LA, LB, LC, LD>(den, geo.sh_bf[sa], geo.sh_bf[sb], geo.sh_bf[sc], geo.sh_bf[sd], scale, gd, gdl);
+        for (int k = 0; k < NAB * NCD; ++k) {
+            gam[k] = (float)gd[k];
+            gaml[k] = (float)gdl[k];
+        }
+    }
+    const bool lr = den.use_lr;
+    const double om2 = den.omega * den.omega;
+    const bool ominf = isinf(den.omega);
+
+    const double *xa = geo.xyz + 3 * geo.sh_atom[sa], *xb = geo.xyz + 3 * geo.sh_atom[sb];
+    const double *xc = geo.xyz + 3 * geo.sh_atom[sc], *xd = geo.xyz + 3 * geo.sh_atom[sd];
+
+    double gA[3] = {0, 0, 0}, gC[3] = {0, 0, 0}, gT[3] = {0, 0, 0};
+
+    for (int ib = 0; ib < nbp; ++ib) {
+        const int ip = pb0 + ib;
+        const double p = pp.p[ip], Px = pp.Px[ip], Py = pp.Py[ip], Pz = pp.Pz[ip], Kab = pp.K[ip];
+        const float za2 = 2.0f * pp.fza[ip];
+        const float oo2p = (float)(0.5 / p);
+        float Ebx[LA + 2][LB + 1][L1 + 2], Eby[LA + 2][LB + 1][L1 + 2], Ebz[LA + 2][LB + 1][L1 + 2];
+        etab<LA + 1, LB>(Ebx, (float)(Px - xa[0]), (float)(Px - xb[0]), oo2p);
+        etab<LA + 1, LB>(Eby, (float)(Py - xa[1]), (float)(Py - xb[1]), oo2p);
+        etab<LA + 1, LB>(Ebz, (float)(Pz - xa[2]), (float)(Pz - xb[2]), oo2p);
+
+        float Fa[NCD][NH1], Fl[NCD][NH1];
+#pragma unroll
+        for (int k = 0; k < NCD; ++k)
+#pragma unroll
+            for (int h = 0; h < NH1; ++h) {
+                Fa[k][h] = 0.0f;
+                Fl[k][h] = 0.0f;
+            }
+        {
+            int ab = 0;
+            for_pairs<LA, LB, UAB>([&](int ax, int ay, int az, int bx, int by, int bz) {
+                for (int t = 0; t <= ax + bx; ++t)
+                    for (int u = 0; u <= ay + by; ++u)
+                        for (int v = 0; v <= az + bz; ++v) {
+                            const float e = Ebx[ax][bx][t] * Eby[ay][by][u] * Ebz[az][bz][v];
+                            const int h = hidx(t, u, v);
+#pragma unroll
+                            for (int k = 0; k < NCD; ++k) {
+                                Fa[k][h] += gam[ab * NCD + k] * e;
+                                if (lr) Fl[k][h] += gaml[ab * NCD + k] * e;
+                            }
+                        }
+                ++ab;
+            });
+        }
+
+        float fA[3] = {0.f, 0.f, 0.f}, fC[3] = {0.f, 0.f, 0.f}, fT[3] = {0.f, 0.f, 0.f};
+        for (int jk = 0; jk < nkp; ++jk) {
+            const int kp = pk0 + jk;
+            const double q = pp.p[kp], Qx = pp.Px[kp], Qy = pp.Py[kp], Qz = pp.Pz[kp], Kcd = pp.K[kp];
+            const float zc2 = 2.0f * pp.fza[kp];
+            const float oo2q = (float)(0.5 / q);
+            float Ekx[LC + 2][LD + 1][L2 + 2], Eky[LC + 2][LD + 1][L2 + 2], Ekz[LC + 2][LD + 1][L2 + 2];
+            etab<LC + 1, LD>(Ekx, (float)(Qx - xc[0]), (float)(Qx - xd[0]), oo2q);
+            etab<LC + 1, LD>(Eky, (float)(Qy - xc[1]), (float)(Qy - xd[1]), oo2q);
+            etab<LC + 1, LD>(Ekz, (float)(Qz - xc[2]), (float)(Qz - xd[2]), oo2q);
+
+            const double pq = p + q;
+            const double rho = p * q / pq;
+            const double Xd = Px - Qx, Yd = Py - Qy, Zd = Pz - Qz;
+            const double T = rho * (Xd * Xd + Yd * Yd + Zd * Zd);
+            const float sc_ = (float)sqrt(2.0 * rho);
+            const float pref = (float)(34.986836655249725 / (p * q * sqrt(pq)) * Kab * Kcd);
+            float spow[L + 3];
+            spow[0] = 1.0f;
+#pragma unroll
+            for (int n = 1; n <= L + 2; ++n) spow[n] = spow[n - 1] * sc_;
+            float R[NR], Rl[NR];
+            {
+                float Fm[L + 2], base[L + 2];
+                boys_mixed<L + 1>(T, Fm, boys);
+#pragma unroll
+                for (int n = 0; n <= L + 1; ++n) base[n] = (n & 1) ? -pref * Fm[n] : pref * Fm[n];
+                hermite_R<L + 1>(R, base, (float)Xd * sc_, (float)Yd * sc_, (float)Zd * sc_);
+                if (lr) {
+                    const double th2 = ominf ? 1.0 : om2 / (om2 + rho);
+                    boys_mixed<L + 1>(T * th2, Fm, boys);
+                    float f = pref * (float)sqrt(th2);
+                    const float t2 = (float)th2;
+#pragma unroll
+                    for (int n = 0; n <= L + 1; ++n) {
+                        base[n] = (n & 1) ? -f * Fm[n] : f * Fm[n];
+                        f *= t2;
+                    }
+                    hermite_R<L + 1>(Rl, base, (float)Xd * sc_, (float)Yd * sc_, (float)Zd * sc_);
+                }
+            }
+
+            float E3k[NCD][NH2];
+            {
+                int cd = 0;
+                for_pairs<LC, LD, true>([&](int cx, int cy, int cz, int dx, int dy, int dz) {
+#pragma unroll
+                    for (int h = 0; h < NH2; ++h) E3k[cd][h] = 0.0f;
+#pragma unroll
+                    for (int t = 0; t <= cx + dx; ++t)
+#pragma unroll
+                        for (int u = 0; u <= cy + dy; ++u)
+#pragma unroll
+                            for (int v = 0; v <= cz + dz; ++v)
+                                E3k[cd][hidx(t, u, v)] =
+                                    Ekx[cx][dx][t] * Eky[cy][dy][u] * Ekz[cz][dz][v] * spow[t + u + v];
+                    ++cd;
+                });
+            }
+
+            {
+                int ab = 0;
+                for_pairs<LA, LB, UAB>([&](int ax, int ay, int az, int bx, int by, int bz) {
+                    float gr[NH2], grl[NH2];
+#pragma unroll 1
+                    for (int h = 0; h < NH2; ++h) {
+                        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < NCD; ++k) {
+                            s0 += gam[ab * NCD + k] * E3k[k][h];
+                            if (lr) s1 += gaml[ab * NCD + k] * E3k[k][h];
+                        }
+                        gr[h] = s0;
+                        grl[h] = s1;
+                    }
+                    float y[NH1P];
+#pragma unroll
+                    for (int h = 0; h < NH1P; ++h) y[h] = 0.0f;
+#pragma unroll 1
+                    for (int t2 = 0; t2 <= L2; ++t2)
+#pragma unroll 1
+                        for (int u2 = 0; u2 <= L2 - t2; ++u2)
+#pragma unroll 1
+                            for (int v2 = 0; v2 <= L2 - t2 - u2; ++v2) {
+                                const int h2 = hidx(t2, u2, v2);
+                                const float sg = ((t2 + u2 + v2) & 1) ? -1.0f : 1.0f;
+                                const float c0 = sg * gr[h2], c1 = sg * grl[h2];
+#pragma unroll
+                                for (int t1 = 0; t1 <= L1 + 1; ++t1)
+#pragma unroll
+                                    for (int u1 = 0; u1 <= L1 + 1 - t1; ++u1)
+#pragma unroll
+                                        for (int v1 = 0; v1 <= L1 + 1 - t1 - u1; ++v1) {
+                                            const int hr = hidx(t1 + t2, u1 + u2, v1 + v2);
+                                            float acc = y[hidx(t1, u1, v1)] + c0 * R[hr];
+                                            if (lr) acc += c1 * Rl[hr];
+                                            y[hidx(t1, u1, v1)] = acc;
+                                        }
+                            }
+#pragma unroll
+                    for (int t1 = 0; t1 <= L1 + 1; ++t1)
+#pragma unroll
+                        for (int u1 = 0; u1 <= L1 + 1 - t1; ++u1)
+#pragma unroll
+                            for (int v1 = 0; v1 <= L1 + 1 - t1 - u1; ++v1) y[hidx(t1, u1, v1)] *= spow[t1 + u1 + v1];
+                    const int nx = ax + bx, ny = ay + by, nz = az + bz;
+                    float sz[L1 + 2][L1 + 2];
+                    for (int t = 0; t <= nx + 1; ++t)
+                        for (int u = 0; u <= ny + 1 && t + u <= L1 + 1; ++u) {
+                            float acc = 0.0f;
+                            for (int v = 0; v <= nz && t + u + v <= L1 + 1; ++v) acc += Ebz[az][bz][v] * y[hidx(t, u, v)];
+                            sz[t][u] = acc;
+                        }
+                    float ax_ = 0.f, ay_ = 0.f, az_ = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+                    for (int t = 0; t <= nx + 1; ++t) {
+                        const float dxt = za2 * Ebx[ax + 1][bx][t] - (ax > 0 ? ax * Ebx[ax - 1][bx][t] : 0.0f);
+                        float s = 0.0f;
+                        for (int u = 0; u <= ny; ++u) s += Eby[ay][by][u] * sz[t][u];
+                        ax_ += dxt * s;
+                    }
+                    for (int t = 0; t <= nx; ++t) {
+                        const float ext = Ebx[ax][bx][t];
+                        float sy = 0.f, sx1 = 0.f, sy1 = 0.f, szd = 0.f, sz1 = 0.f;
+                        for (int u = 0; u <= ny + 1; ++u) {
+                            const float dyu = za2 * Eby[ay + 1][by][u] - (ay > 0 ? ay * Eby[ay - 1][by][u] : 0.0f);
+                            sy += dyu * sz[t][u];
+                        }
+                        for (int u = 0; u <= ny; ++u) {
+                            const float eyu = Eby[ay][by][u];
+                            sx1 += eyu * sz[t + 1][u];
+                            sy1 += eyu * sz[t][u + 1];
+                            float a1 = 0.f, a2 = 0.f;
+                            for (int v = 0; v <= nz + 1; ++v) {
+                                const float dzv = za2 * Ebz[az + 1][bz][v] - (az > 0 ? az * Ebz[az - 1][bz][v] : 0.0f);
+                                a1 += dzv * y[hidx(t, u, v)];
+                            }
+                            for (int v = 0; v <= nz; ++v) a2 += Ebz[az][bz][v] * y[hidx(t, u, v + 1)];
+                            szd += eyu * a1;
+                            sz1 += eyu * a2;
+                        }
+                        ay_ += ext * sy;
+                        az_ += ext * szd;
+                        tx += ext * sx1;
+                        ty += ext * sy1;
+                        tz += ext * sz1;
+                    }
+                    fA[0] += ax_;
+                    fA[1] += ay_;
+                    fA[2] += az_;
+                    fT[0] += tx;
+                    fT[1] += ty;
+                    fT[2] += tz;
+                    ++ab;
+                });
+            }
+
+            {
+                int cd = 0;
+                for_pairs<LC, LD, UCD>([&](int cx, int cy, int cz, int dx, int dy, int dz) {
+                    float z[NH2P];
+#pragma unroll
+                    for (int h = 0; h < NH2P; ++h) z[h] = 0.0f;
+#pragma unroll 1
+                    for (int t1 = 0; t1 <= L1; ++t1)
+#pragma unroll 1
+                        for (int u1 = 0; u1 <= L1 - t1; ++u1)
+#pragma unroll 1
+                            for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
+                                const int h1 = hidx(t1, u1, v1);
+                                const float sh = spow[t1 + u1 + v1];
+                                const float f0 = Fa[cd][h1] * sh, f1 = Fl[cd][h1] * sh;
+#pragma unroll
+                                for (int t2 = 0; t2 <= L2 + 1; ++t2)
+#pragma unroll
+                                    for (int u2 = 0; u2 <= L2 + 1 - t2; ++u2)
+#pragma unroll
+                                        for (int v2 = 0; v2 <= L2 + 1 - t2 - u2; ++v2) {
+                                            const int hr = hidx(t1 + t2, u1 + u2, v1 + v2);
+                                            float acc = z[hidx(t2, u2, v2)] + f0 * R[hr];
+                                            if (lr) acc += f1 * Rl[hr];
+                                            z[hidx(t2, u2, v2)] = acc;
+                                        }
+                            }
+                    const int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+#pragma unroll
+                    for (int t2 = 0; t2 <= L2 + 1; ++t2)
+#pragma unroll
+                        for (int u2 = 0; u2 <= L2 + 1 - t2; ++u2)
+#pragma unroll
+                            for (int v2 = 0; v2 <= L2 + 1 - t2 - u2; ++v2) {
+                                const float w = spow[t2 + u2 + v2];
+                                z[hidx(t2, u2, v2)] *= ((t2 + u2 + v2) & 1) ? -w : w;
+                            }
+                    float sz[L2 + 2][L2 + 2];
+                    for (int t = 0; t <= nx + 1; ++t)
+                        for (int u = 0; u <= ny + 1 && t + u <= L2 + 1; ++u) {
+                            float acc = 0.0f;
+                            for (int v = 0; v <= nz && t + u + v <= L2 + 1; ++v) acc += Ekz[cz][dz][v] * z[hidx(t, u, v)];
+                            sz[t][u] = acc;
+                        }
+                    float cx_ = 0.f, cy_ = 0.f, cz_ = 0.f;
+                    for (int t = 0; t <= nx + 1; ++t) {
+                        const float dxt = zc2 * Ekx[cx + 1][dx][t] - (cx > 0 ? cx * Ekx[cx - 1][dx][t] : 0.0f);
+                        float s = 0.0f;
+                        for (int u = 0; u <= ny; ++u) s += Eky[cy][dy][u] * sz[t][u];
+                        cx_ += dxt * s;
+                    }
+                    for (int t = 0; t <= nx; ++t) {
+                        const float ext = Ekx[cx][dx][t];
+                        float sy = 0.f, szd = 0.f;
+                        for (int u = 0; u <= ny + 1; ++u) {
+                            const float dyu = zc2 * Eky[cy + 1][dy][u] - (cy > 0 ? cy * Eky[cy - 1][dy][u] : 0.0f);
+                            sy += dyu * sz[t][u];
+                        }
+                        for (int u = 0; u <= ny; ++u) {
+                            float a1 = 0.f;
+                            for (int v = 0; v <= nz + 1; ++v) {
+                                const float dzv = zc2 * Ekz[cz + 1][dz][v] - (cz > 0 ? cz * Ekz[cz - 1][dz][v] : 0.0f);
+                                a1 += dzv * z[hidx(t, u, v)];
+                            }
+                            szd += Eky[cy][dy][u] * a1;
+                        }
+                        cy_ += ext * sy;
+                        cz_ += ext * szd;
+                    }
+                    fC[0] += cx_;
+                    fC[1] += cy_;
+                    fC[2] += cz_;
+                    ++cd;
+                });
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            gA[i] += (double)fA[i];
+            gC[i] += (double)fC[i];
+            gT[i] += (double)fT[i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g[i] = gA[i];
+        g[3 + i] = gT[i] - gA[i];
+        g[6 + i] = gC[i];
+        g[9 + i] = -gT[i] - gC[i];
+    }
+}
+
+// Per-quartet screening bound (see tdgrad.h) and shard membership.
+__device__ __forceinline__ bool keep_quartet(const ScreenArgs &scr, const PairSet &bra, const PairSet &ket, int bi,
+                                             int ki, int sa, int sb, int sc, int sd)
+{
+    if (scr.nranks > 1) {
+        const int key = max(bra.key[bi], ket.key[ki]);
+        if (key % scr.nranks != scr.rank) return false;
+    }
+    if (scr.tau > 0.0) {
+        const double S = fmax(bra.Qd[bi] * ket.Q[ki], bra.Q[bi] * ket.Qd[ki]);
+        const int ns = scr.nshell;
+        const double *M = scr.M;
+        double Mq = M[(size_t)sa * ns + sb];
+        Mq = fmax(Mq, M[(size_t)sc * ns + sd]);
+        Mq = fmax(Mq, M[(size_t)sa * ns + sc]);
+        Mq = fmax(Mq, M[(size_t)sa * ns + sd]);
+        Mq = fmax(Mq, M[(size_t)sb * ns + sc]);
+        Mq = fmax(Mq, M[(size_t)sb * ns + sd]);
+        const double bound = scr.scale * S * Mq * Mq;
+        if (bound < scr.tau) return false;
+    }
+    return true;
+}
+
+// Persistent class kernel: CTA c takes tiles c, c+G, c+2G, ... of its class;
+// every tile's 12 x TILE gradient contributions are added to the CTA's
+// partial gradient in a fixed order, so results are bitwise reproducible.
+template <int LA, int LB, int LC, int LD, bool FP32>
+__global__ void __launch_bounds__(TILE) k_grad(GeoArgs geo, DensArgs den, ScreenArgs scr, ClassLaunch cl,
+                                               OutArgs out, PrimPairs pp, const double *__restrict__ boys)
+{
+    extern __shared__ double smem[];
+    const int natom3 = geo.natom * 3;
+    double *sg = out.use_smem ? smem : out.partials + (size_t)blockIdx.x * natom3;
+    double *stg = smem + (out.use_smem ? natom3 : 0);
+    int *sat = reinterpret_cast<int *>(stg + TILE * 12);
+    if (out.use_smem) {
+        for (int k = threadIdx.x; k < natom3; k += blockDim.x) sg[k] = 0.0;
+    }
+    __syncthreads();
+    unsigned long long nq = 0, npq = 0;
+    for (long long it = blockIdx.x; it < cl.ntiles; it += gridDim.x) {
+        const uint2 tl = cl.tiles[it];
+        const int bi = tl.x * TB + threadIdx.x / TK;
+        const int ki = tl.y * TK + threadIdx.x % TK;
+        double g[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) g[k] = 0.0;
+        int at[4] = {-1, -1, -1, -1};
+        bool ok = bi < cl.bra.n && ki < cl.ket.n && (!cl.same || bi >= ki);
+        if (ok) {
+            const int sa = cl.bra.sa[bi], sb = cl.bra.sb[bi], sc = cl.ket.sa[ki], sd = cl.ket.sb[ki];
+            ok = keep_quartet(scr, cl.bra, cl.ket, bi, ki, sa, sb, sc, sd);
+            if (ok) {
+                double scale = 1.0;
+                if (sa == sb) scale *= 0.5;
+                if (sc == sd) scale *= 0.5;
+                if (cl.same && bi == ki) scale *= 0.5;
+                const int nbp = cl.bra.np[bi], nkp = cl.ket.np[ki];
+                if constexpr (FP32)
+                    quartet_fp32<LA, LB, LC, LD>(geo, den, pp, sa, sb, sc, sd, cl.bra.poff[bi], nbp, cl.ket.poff[ki],
+                                                 nkp, scale, boys, g);
+                else
+                    quartet_fp64<LA, LB, LC, LD>(geo, den, pp, sa, sb, sc, sd, cl.bra.poff[bi], nbp, cl.ket.poff[ki],
+                                                 nkp, scale, boys, g);
+                at[0] = geo.sh_atom[sa];
+                at[1] = geo.sh_atom[sb];
+                at[2] = geo.sh_atom[sc];
+                at[3] = geo.sh_atom[sd];
+                nq += 1;
+                npq += (unsigned long long)nbp * nkp;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) stg[threadIdx.x * 12 + k] = g[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sat[threadIdx.x * 4 + k] = at[k];
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const int i = threadIdx.x;
+            for (int t = 0; t < TILE; ++t)
+#pragma unroll
+                for (int X = 0; X < 4; ++X) {
+                    const int a = sat[t * 4 + X];
+                    if (a >= 0) sg[a * 3 + i] += stg[t * 12 + X * 3 + i];
+                }
+        }
+        __syncthreads();
+    }
+    if (out.use_smem) {
+        double *dst = out.partials + (size_t)blockIdx.x * natom3;
+        for (int k = threadIdx.x; k < natom3; k += blockDim.x) dst[k] += sg[k];
+    }
+    // counters
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nq += __shfl_xor_sync(0xffffffffu, nq, o);
+        npq += __shfl_xor_sync(0xffffffffu, npq, o);
+    }
+    if ((threadIdx.x & 31) == 0 && nq) {
+        atomicAdd(out.counters + 0, nq);
+        atomicAdd(out.counters + 1, npq);
+        if (FP32) atomicAdd(out.counters + 2, nq);
+    }
+}
+
+template <int LA, int LB, int LC, int LD>
+cudaError_t launch_class_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const GeoArgs &geo,
+                                const DensArgs &den, const ScreenArgs &scr, const ClassLaunch &cl, const OutArgs &out,
+                                const PrimPairs &pp, const double *boys)
+{
+    auto kern = fp32 ? k_grad<LA, LB, LC, LD, true> : k_grad<LA, LB, LC, LD, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, TILE, smem, st>>>(geo, den, scr, cl, out, pp, boys);
+    return cudaGetLastError();
+}
+
+}  // namespace tg
