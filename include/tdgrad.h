@@ -65,6 +65,7 @@ extern "C" {
 #define TG_FP64 0             /* every primitive quartet in fp64 */
 #define TG_MIXED_BOUND 1      /* fp32/fp64 routing by the rigorous bound */
 #define TG_MIXED_LEARNED 2    /* fp32/fp64 routing by the learned router */
+#define TG_FP32 3             /* every primitive quartet in fp32 (no accuracy target; calibration) */
 
 #define TG_MAX_PAIRS 8
 
@@ -80,7 +81,10 @@ typedef struct {
 
 typedef struct {
     double screen_tol;      /* density-multiplied Schwarz threshold; default 1e-10 (Sec. II.E) */
-    int precision;          /* TG_FP64 (default), TG_MIXED_BOUND, TG_MIXED_LEARNED */
+    int precision;          /* TG_FP64 (default), TG_MIXED_BOUND, TG_MIXED_LEARNED, TG_FP32.
+                               Mixed modes run a tile in fp32 only while the summed error
+                               estimate of all fp32 tiles stays below mixed_tol; gradient
+                               accumulation and the reduction are always fp64. */
     const tg_router *router;/* required for TG_MIXED_LEARNED */
     double mixed_tol;       /* target max |dg| of the fp32 route, default 1e-6 Ha/bohr */
     int device_ptrs;        /* 1: A, B and grad are device pointers */
@@ -125,6 +129,43 @@ int tg_grad2e(const tg_basis *b, int npair, const tg_pair *pairs, const tg_optio
               double *grad, tg_stats *stats);
 
 const char *tg_strerror(int status);
+
+/* ---- learned block router (fp32 / fp64 routing only; it never skips work)
+ * A 16-32-32-1 tanh perceptron maps 16 features of a quartet tile (angular
+ * class, log10 of the tile's Schwarz x density bound, of Q and Q' on each
+ * side, of the cross and pair density factors, pair-centre distances, pair
+ * extents, smallest exponent sums, primitive-pair counts) to the log10 of the
+ * tile's largest gradient contribution.  TG_MIXED_LEARNED routes a tile to
+ * fp32 while the summed estimate eps_rel * 128 * 10^(prediction + margin)
+ * stays within mixed_tol.  The paper has no counterpart: its kernels are
+ * fp64 throughout (Sec. II.C, II.E). */
+
+/* Per-tile training data: every stride-th screened tile (at most cap) of the
+ * call's workload is evaluated in fp64 and in fp32 without reduction.
+ * features: cap*16; target: log10 max |fp64 contribution| over the tile;
+ * err32: log10 max |fp32 - fp64| over the tile; *n_out: tiles written. */
+int tg_tile_samples(const tg_basis *b, int npair, const tg_pair *pairs, const tg_options *opt, int stride, int cap,
+                    float *features, float *target, float *err32, int *n_out);
+
+int tg_router_nparam(void);                         /* 1633 */
+int tg_router_create(unsigned long long seed, tg_router **out);  /* Xavier-uniform init */
+void tg_router_destroy(tg_router *r);
+/* params: tg_router_nparam() floats (W1[32][16], b1, W2[32][32], b2, w3[32], b3);
+ * mu, sd: 16 feature means / standard deviations; calib: {margin, eps_rel, trained}.
+ * Any pointer may be NULL. */
+int tg_router_get(const tg_router *r, float *params, float *mu, float *sd, float *calib);
+int tg_router_set(tg_router *r, const float *params, const float *mu, const float *sd, const float *calib);
+/* GPU training: standardise the features, then `epochs` full-batch Adam steps
+ * on the expectile loss mean(w r^2), r = y - yhat, w = q if r > 0 else 1-q.
+ * X: n*16 host floats, y: n; loss_hist (nullable): epochs floats. */
+int tg_router_train(tg_router *r, int n, const float *X, const float *y, int epochs, float lr, float q,
+                    float *loss_hist);
+/* Loss and gradient (tg_router_nparam() floats) of the current parameters. */
+int tg_router_loss_grad(const tg_router *r, int n, const float *X, const float *y, float q, float *loss,
+                        float *grad);
+int tg_router_predict(const tg_router *r, int n, const float *X, float *out);
+int tg_router_save(const tg_router *r, const char *path);
+int tg_router_load(const char *path, tg_router **out);
 
 #ifdef __cplusplus
 }

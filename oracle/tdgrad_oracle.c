@@ -41,7 +41,12 @@
  *      M(x,y)= max_p sqrt(|c_J|+|c_K|+|c_K_lr|) max(|A_p|,|B_p|) over the
  *              shell blocks (x,y) and (y,x),
  *      M_q   = max of M over the blocks ab, cd, ac, ad, bc, bd.
- *    tau = 0 keeps every quartet (no approximation at all).
+ *    With tau > 0 a primitive pair (k,l) of a shell pair is also dropped iff
+ *      8 * npair * b_kl * max(Qmax, Q'max) * Mmax^2 < 1e-6 tau,
+ *      b_kl = max over mu nu and over the plain and derivative charges of
+ *             |c_k c_l| sqrt(self-repulsion) (the terms summed in Q and Q'),
+ *    with Qmax, Q'max, Mmax the largest Q, Q', M of the system.
+ *    tau = 0 keeps every quartet and primitive (no approximation at all).
  *  - Shards: a quartet belongs to shard (rank, nranks) iff
  *      max(key(a,b), key(c,d)) mod nranks == rank,
  *      key(x,y) = X(X+1)/2 + Y with X = max(x,y), Y = min(x,y).
@@ -349,7 +354,8 @@ static void ws_free(quartet_ws *q)
  * (op 0 = Coulomb; op 1 = erf with omega) into q->T.  deriv selects whether
  * the extents include the +1 needed by derivatives and the 2 zeta weights. */
 static void contract_tables(const obasis *bs, quartet_ws *q, int sa, int sb, int sc, int sd,
-                            int nops, const double *omegas, int deriv)
+                            int nops, const double *omegas, int deriv, const unsigned char *keep_ab,
+                            const unsigned char *keep_cd)
 {
     int la = bs->sh_l[sa], lb = bs->sh_l[sb], lc = bs->sh_l[sc], ld = bs->sh_l[sd];
     int Le = la + lb + deriv, Lf = lc + ld + deriv;
@@ -368,6 +374,8 @@ static void contract_tables(const obasis *bs, quartet_ws *q, int sa, int sb, int
         for (int kb = 0; kb < bs->sh_nprim[sb]; ++kb)
             for (int kc = 0; kc < bs->sh_nprim[sc]; ++kc)
                 for (int kd = 0; kd < bs->sh_nprim[sd]; ++kd) {
+                    if (keep_ab && !keep_ab[ka * bs->sh_nprim[sb] + kb]) continue;
+                    if (keep_cd && !keep_cd[kc * bs->sh_nprim[sd] + kd]) continue;
                     double za = bs->exps[bs->sh_off[sa] + ka], zb = bs->exps[bs->sh_off[sb] + kb];
                     double zc = bs->exps[bs->sh_off[sc] + kc], zd = bs->exps[bs->sh_off[sd] + kd];
                     double cc = bs->cn[bs->sh_off[sa] + ka] * bs->cn[bs->sh_off[sb] + kb] *
@@ -427,7 +435,7 @@ void or_shell_eri(int natom, const double *xyz, int nshell, const int *sh_atom, 
     quartet_ws q;
     ws_alloc(&q);
     double om[1] = {omega};
-    contract_tables(&bs, &q, sa, sb, sc, sd, 1, om, 0);
+    contract_tables(&bs, &q, sa, sb, sc, sd, 1, om, 0, NULL, NULL);
     const double *A = xyz + 3 * sh_atom[sa], *B = xyz + 3 * sh_atom[sb];
     const double *C = xyz + 3 * sh_atom[sc], *D = xyz + 3 * sh_atom[sd];
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]}, CD[3] = {C[0] - D[0], C[1] - D[1], C[2] - D[2]};
@@ -455,7 +463,7 @@ void or_shell_eri_deriv(int natom, const double *xyz, int nshell, const int *sh_
     quartet_ws q;
     ws_alloc(&q);
     double om[1] = {omega};
-    contract_tables(&bs, &q, sa, sb, sc, sd, 1, om, 1);
+    contract_tables(&bs, &q, sa, sb, sc, sd, 1, om, 1, NULL, NULL);
     const double *A = xyz + 3 * sh_atom[sa], *B = xyz + 3 * sh_atom[sb];
     const double *C = xyz + 3 * sh_atom[sc], *D = xyz + 3 * sh_atom[sd];
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]}, CD[3] = {C[0] - D[0], C[1] - D[1], C[2] - D[2]};
@@ -479,7 +487,7 @@ void or_shell_eri_deriv(int natom, const double *xyz, int nshell, const int *sh_
 
 /* ------------------------------------------------------------- Schwarz */
 /* Q_ab and Q'_ab (see header comment) from primitive self-repulsions. */
-static void schwarz_pair(const obasis *bs, quartet_ws *q, int sa, int sb, double *Qo, double *Qdo)
+static void schwarz_pair(const obasis *bs, quartet_ws *q, int sa, int sb, double *Qo, double *Qdo, double *bprim)
 {
     int la = bs->sh_l[sa], lb = bs->sh_l[sb];
     int na = ncart(la), nb = ncart(lb);
@@ -498,11 +506,13 @@ static void schwarz_pair(const obasis *bs, quartet_ws *q, int sa, int sb, double
             double *T = q->T[0][0][0];
             for (int e = 0; e < tri_start[L + 1]; ++e)
                 for (int f = 0; f < tri_start[L + 1]; ++f) T[e * OR_NTRI + f] = q->w.V[VIX(e, f, 0)];
+            double bmax = 0.0;
             for (int a = 0; a < na; ++a)
                 for (int b = 0; b < nb; ++b) {
                     int ta = tri_start[la] + a, tb = tri_start[lb] + b;
                     double s = hrr(T, r, ta, tb, ta, tb, AB, AB);
                     acc[a * nb + b] += cc * sqrt(s > 0 ? s : 0.0);
+                    if (cc * sqrt(s > 0 ? s : 0.0) > bmax) bmax = cc * sqrt(s > 0 ? s : 0.0);
                     for (int X = 0; X < 2; ++X)
                         for (int i = 0; i < 3; ++i) {
                             /* derivative function on centre X: 2z (+1_i) - n (-1_i) */
@@ -521,8 +531,10 @@ static void schwarz_pair(const obasis *bs, quartet_ws *q, int sa, int sb, double
                                     v += cf[u] * cf[w] * hrr(T, r, a1, b1, a2, b2, AB, AB);
                                 }
                             accd[(a * nb + b) * 6 + X * 3 + i] += cc * sqrt(v > 0 ? v : 0.0);
+                            if (cc * sqrt(v > 0 ? v : 0.0) > bmax) bmax = cc * sqrt(v > 0 ? v : 0.0);
                         }
                 }
+            if (bprim) bprim[ka * bs->sh_nprim[sb] + kb] = bmax;
         }
     double Q = 0.0, Qd = 0.0;
     for (int n = 0; n < na * nb; ++n) if (acc[n] > Q) Q = acc[n];
@@ -546,7 +558,7 @@ void or_schwarz(int natom, const double *xyz, int nshell, const int *sh_atom, co
         for (int a = 0; a < nshell; ++a)
             for (int b = 0; b <= a; ++b) {
                 double x, y;
-                schwarz_pair(&bs, &q, a, b, &x, &y);
+                schwarz_pair(&bs, &q, a, b, &x, &y, NULL);
                 Q[a * nshell + b] = Q[b * nshell + a] = x;
                 Qd[a * nshell + b] = Qd[b * nshell + a] = y;
             }
@@ -589,7 +601,8 @@ static inline void gamma_ordered(const opairs *pp, int nbf, int m, int n, int l,
 /* Process one shell quartet (sa sb | sc sd): gamma from the given function
  * (ordered or 8-image) rule, derivative integrals, scatter to atoms. */
 static void do_quartet(const obasis *bs, quartet_ws *q, const opairs *pp, int sa, int sb, int sc, int sd,
-                       int canonical, double scale, double *grad, double *energy, int want_grad)
+                       int canonical, double scale, double *grad, double *energy, int want_grad,
+                       const unsigned char *keep_ab, const unsigned char *keep_cd)
 {
     int la = bs->sh_l[sa], lb = bs->sh_l[sb], lc = bs->sh_l[sc], ld = bs->sh_l[sd];
     int na = ncart(la), nb = ncart(lb), nc = ncart(lc), nd = ncart(ld);
@@ -597,7 +610,7 @@ static void do_quartet(const obasis *bs, quartet_ws *q, const opairs *pp, int sa
     int nbf = bs->nbf;
     int nops = pp->use_lr ? 2 : 1;
     double omegas[2] = {0.0, pp->omega};
-    contract_tables(bs, q, sa, sb, sc, sd, nops, omegas, want_grad);
+    contract_tables(bs, q, sa, sb, sc, sd, nops, omegas, want_grad, keep_ab, keep_cd);
     const double *A = bs->xyz + 3 * bs->sh_atom[sa], *B = bs->xyz + 3 * bs->sh_atom[sb];
     const double *C = bs->xyz + 3 * bs->sh_atom[sc], *D = bs->xyz + 3 * bs->sh_atom[sd];
     double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]}, CD[3] = {C[0] - D[0], C[1] - D[1], C[2] - D[2]};
@@ -709,6 +722,45 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
         }
         free(tmp);
     }
+    /* primitive-pair keep masks (tau > 0) */
+    unsigned char *keep = NULL;
+    long long *keep_off = NULL;
+    if (mode == 1 && tau > 0) {
+        long long npr = (long long)ns * (ns + 1) / 2;
+        keep_off = (long long *)malloc(sizeof(long long) * (npr + 1));
+        long long o = 0;
+        for (int a = 0; a < ns; ++a)
+            for (int b = 0; b <= a; ++b) {
+                keep_off[(long long)a * (a + 1) / 2 + b] = o;
+                o += (long long)sh_nprim[a] * sh_nprim[b];
+            }
+        keep_off[npr] = o;
+        keep = (unsigned char *)malloc(o > 0 ? o : 1);
+        double qmax = 0.0, qdmax = 0.0, mmax = 0.0;
+        for (int k = 0; k < ns * ns; ++k) {
+            if (Q[k] > qmax) qmax = Q[k];
+            if (Qd[k] > qdmax) qdmax = Qd[k];
+            if (Mb[k] > mmax) mmax = Mb[k];
+        }
+        double qq = qmax > qdmax ? qmax : qdmax;
+        double eps_p = 1e-6 * tau;
+#pragma omp parallel
+        {
+            quartet_ws qw;
+            ws_alloc(&qw);
+            double bp[256];
+#pragma omp for schedule(dynamic, 4)
+            for (int a = 0; a < ns; ++a)
+                for (int b = 0; b <= a; ++b) {
+                    double x, y;
+                    schwarz_pair(&bs, &qw, a, b, &x, &y, bp);
+                    long long o2 = keep_off[(long long)a * (a + 1) / 2 + b];
+                    for (int k = 0; k < sh_nprim[a] * sh_nprim[b]; ++k)
+                        keep[o2 + k] = (8.0 * npair * bp[k] * qq * mmax * mmax < eps_p) ? 0 : 1;
+                }
+            ws_free(&qw);
+        }
+    }
 
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -737,7 +789,7 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
                     for (int c = 0; c < ns; ++c)
                         for (int d = 0; d < ns; ++d) {
                             do_quartet(&bs, &q, &pp, a, b, c, d, 0, 1.0, gacc + (size_t)t * natom * 3,
-                                       Ep ? Ep + t : NULL, want_grad);
+                                       Ep ? Ep + t : NULL, want_grad, NULL, NULL);
                             cnt[t]++;
                         }
             ws_free(&q);
@@ -778,7 +830,8 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
                         if (c == d) scale *= 0.5;
                         if (ab == cd) scale *= 0.5;
                         do_quartet(&bs, &q, &pp, a, b, c, d, 1, scale, gacc + (size_t)t * natom * 3,
-                                   Ep ? Ep + t : NULL, want_grad);
+                                   Ep ? Ep + t : NULL, want_grad, keep ? keep + keep_off[ab] : NULL,
+                                   keep ? keep + keep_off[cd] : NULL);
                         cnt[t]++;
                     }
             }
@@ -802,7 +855,7 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
         *nquart_out = s;
     }
     free(gacc); free(eacc); free(cnt); free(cKlr_eff);
-    free(Q); free(Qd); free(Mb);
+    free(Q); free(Qd); free(Mb); free(keep); free(keep_off);
     basis_free(&bs);
     return 0;
 }

@@ -29,10 +29,14 @@ TG_EROUTER = -6
 TG_FP64 = 0
 TG_MIXED_BOUND = 1
 TG_MIXED_LEARNED = 2
+TG_FP32 = 3
 TG_MAX_PAIRS = 8
 
 EXPORTS = ("tg_options_default", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
-           "tg_grad2e", "tg_strerror")
+           "tg_grad2e", "tg_strerror", "tg_tile_samples", "tg_router_nparam", "tg_router_create",
+           "tg_router_destroy", "tg_router_get", "tg_router_set", "tg_router_train", "tg_router_loss_grad",
+           "tg_router_predict", "tg_router_save", "tg_router_load")
+NFEAT = 16
 
 
 class tg_pair(ctypes.Structure):
@@ -94,6 +98,24 @@ def lib():
         L.tg_grad2e.restype = ctypes.c_int
         L.tg_strerror.argtypes = [ctypes.c_int]
         L.tg_strerror.restype = ctypes.c_char_p
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.tg_tile_samples.argtypes = [vp, ctypes.c_int, ctypes.POINTER(tg_pair), ctypes.POINTER(tg_options),
+                                      ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.POINTER(ctypes.c_int)]
+        L.tg_router_nparam.argtypes = []
+        L.tg_router_create.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(vp)]
+        L.tg_router_destroy.argtypes = [vp]
+        L.tg_router_destroy.restype = None
+        L.tg_router_get.argtypes = [vp, fp, fp, fp, fp]
+        L.tg_router_set.argtypes = [vp, fp, fp, fp, fp]
+        L.tg_router_train.argtypes = [vp, ctypes.c_int, fp, fp, ctypes.c_int, ctypes.c_float, ctypes.c_float, fp]
+        L.tg_router_loss_grad.argtypes = [vp, ctypes.c_int, fp, fp, ctypes.c_float, fp, fp]
+        L.tg_router_predict.argtypes = [vp, ctypes.c_int, fp, fp]
+        L.tg_router_save.argtypes = [vp, ctypes.c_char_p]
+        L.tg_router_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+        for n in ("tg_tile_samples", "tg_router_nparam", "tg_router_create", "tg_router_get", "tg_router_set",
+                  "tg_router_train", "tg_router_loss_grad", "tg_router_predict", "tg_router_save",
+                  "tg_router_load"):
+            getattr(L, n).restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -171,8 +193,34 @@ class Basis:
         except Exception:
             pass
 
+    def _plist(self, pairs):
+        keep, plist = [], []
+        for (a, b, cj, ck, cl, om) in pairs:
+            a, b = _c(a, np.float64), _c(b, np.float64)
+            keep += [a, b]
+            plist.append((a.ctypes.data, b.ctypes.data, float(cj), float(ck), float(cl), float(om)))
+        return keep, plist
+
+    def tile_samples(self, pairs, stride=50, cap=100000, screen_tol=1e-10):
+        """Router training data: (features [n,16], log10 max|fp64 contribution|,
+        log10 max|fp32 - fp64|) for every stride-th screened tile."""
+        keep, plist = self._plist(pairs)
+        arr = (tg_pair * len(plist))(*[tg_pair(*p) for p in plist])
+        opt = tg_options_default()
+        opt.screen_tol = float(screen_tol)
+        X = np.zeros((cap, NFEAT), dtype=np.float32)
+        y = np.zeros(cap, dtype=np.float32)
+        e = np.zeros(cap, dtype=np.float32)
+        n = ctypes.c_int(0)
+        f = ctypes.POINTER(ctypes.c_float)
+        rc = lib().tg_tile_samples(self.h, len(plist), arr, ctypes.byref(opt), int(stride), int(cap),
+                                   X.ctypes.data_as(f), y.ctypes.data_as(f), e.ctypes.data_as(f), ctypes.byref(n))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_tile_samples")
+        return X[:n.value].copy(), y[:n.value].copy(), e[:n.value].copy()
+
     def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
-               timing=False):
+               timing=False, router=None, mixed_tol=1e-6):
         """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
         torch CUDA tensors (then the densities and ``out`` stay on the device)."""
         opt = tg_options_default()
@@ -180,6 +228,9 @@ class Basis:
         opt.precision = int(precision)
         opt.rank, opt.nranks = int(rank), int(nranks)
         opt.timing = 1 if timing else 0
+        opt.mixed_tol = float(mixed_tol)
+        if router is not None:
+            opt.router = router.h
         dev = hasattr(pairs[0][0], "is_cuda") and pairs[0][0].is_cuda
         keep = []
         plist = []
@@ -215,3 +266,85 @@ def grad2e(system, pairs=None, **kw):
         return b.grad2e(system["pairs"] if pairs is None else pairs, **kw)
     finally:
         b.close()
+
+
+class Router:
+    """Owns a tg_router handle (16-32-32-1 tanh MLP trained on the GPU)."""
+
+    def __init__(self, seed=0, path=None):
+        self.h = ctypes.c_void_p()
+        if path is not None:
+            rc = lib().tg_router_load(os.fsencode(path), ctypes.byref(self.h))
+            if rc != TG_OK:
+                raise TGError(rc, "tg_router_load")
+        else:
+            rc = lib().tg_router_create(int(seed), ctypes.byref(self.h))
+            if rc != TG_OK:
+                raise TGError(rc, "tg_router_create")
+        self.nparam = lib().tg_router_nparam()
+
+    def close(self):
+        if self.h is not None:
+            lib().tg_router_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _f(a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+    def get(self):
+        p = np.zeros(self.nparam, np.float32)
+        mu = np.zeros(NFEAT, np.float32)
+        sd = np.zeros(NFEAT, np.float32)
+        cal = np.zeros(3, np.float32)
+        rc = lib().tg_router_get(self.h, self._f(p), self._f(mu), self._f(sd), self._f(cal))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_router_get")
+        return p, mu, sd, cal
+
+    def set(self, params=None, mu=None, sd=None, calib=None):
+        c = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
+        params, mu, sd, calib = c(params), c(mu), c(sd), c(calib)
+        nul = ctypes.POINTER(ctypes.c_float)()
+        rc = lib().tg_router_set(self.h, *[nul if a is None else self._f(a) for a in (params, mu, sd, calib)])
+        if rc != TG_OK:
+            raise TGError(rc, "tg_router_set")
+
+    def train(self, X, y, epochs=300, lr=1e-2, q=0.9):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        hist = np.zeros(epochs, np.float32)
+        rc = lib().tg_router_train(self.h, len(y), self._f(X), self._f(y), int(epochs), float(lr), float(q),
+                                   self._f(hist))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_router_train")
+        return hist
+
+    def loss_grad(self, X, y, q=0.9):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        g = np.zeros(self.nparam, np.float32)
+        L = np.zeros(1, np.float32)
+        rc = lib().tg_router_loss_grad(self.h, len(y), self._f(X), self._f(y), float(q), self._f(L), self._f(g))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_router_loss_grad")
+        return float(L[0]), g
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, np.float32)
+        out = np.zeros(len(X), np.float32)
+        rc = lib().tg_router_predict(self.h, len(X), self._f(X), self._f(out))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_router_predict")
+        return out
+
+    def save(self, path):
+        rc = lib().tg_router_save(self.h, os.fsencode(path))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_router_save")

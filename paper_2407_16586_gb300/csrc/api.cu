@@ -3,6 +3,8 @@
 // the final reduction.  Every arithmetic step of the gradient runs in the
 // CUDA kernels; the host only orders work and moves buffers.
 #include <algorithm>
+#include <cstdio>
+#include <cstdint>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -10,6 +12,7 @@
 #include <vector>
 
 #include "class_launchers.cuh"
+#include "router.cuh"
 #include "setup_kernels.cuh"
 
 using namespace tg;
@@ -49,6 +52,14 @@ inline size_t al(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
 
 }  // namespace
 
+struct tg_router {
+    float params[NPARAM];
+    float mu[NFEAT], sd[NFEAT];
+    float margin = 0.f;   // added to predictions (log10) before routing
+    float eps_rel = 0.f;  // fp32 error of a quartet relative to its largest contribution
+    int trained = 0;
+};
+
 struct tg_basis {
     int device = 0;
     int natom = 0, nshell = 0, nbf = 0, nprim = 0;
@@ -57,7 +68,10 @@ struct tg_basis {
     int *d_sh_atom = nullptr, *d_sh_l = nullptr, *d_sh_nprim = nullptr, *d_sh_poff = nullptr, *d_sh_bf = nullptr;
     std::vector<double> Q, Qd;  // per canonical pair key (x >= y)
     double Qmax = 0.0, Qdmax = 0.0;
-    DevArena ws;
+    long long *d_bpoff = nullptr;  // per canonical pair key: offset of its primitive-pair bounds
+    double *d_bp = nullptr;        // primitive-pair bounds b_kl (larger shell index first)
+    DevArena ws1, ws2;
+    float *d_router = nullptr;  // router parameters, mean and std on the device
     int nsm = 0;
 };
 
@@ -91,7 +105,11 @@ void free_basis(tg_basis *b)
     cudaFree(b->d_sh_nprim);
     cudaFree(b->d_sh_poff);
     cudaFree(b->d_sh_bf);
-    b->ws.release();
+    cudaFree(b->d_router);
+    cudaFree(b->d_bpoff);
+    cudaFree(b->d_bp);
+    b->ws1.release();
+    b->ws2.release();
 }
 
 int basis_setup(tg_basis *b, const double *xyz, const double *exps, const double *coefs)
@@ -104,6 +122,7 @@ int basis_setup(tg_basis *b, const double *xyz, const double *exps, const double
     TG_CUDA(cudaMalloc(&b->d_coefs, sizeof(double) * np));
     TG_CUDA(cudaMalloc(&b->d_cn, sizeof(double) * np));
     TG_CUDA(cudaMalloc(&b->d_boys, sizeof(double) * BOYS_NG * (BOYS_M + 1)));
+    TG_CUDA(cudaMalloc(&b->d_router, sizeof(float) * (NPARAM + 2 * NFEAT)));
     TG_CUDA(cudaMalloc(&b->d_sh_atom, sizeof(int) * ns));
     TG_CUDA(cudaMalloc(&b->d_sh_l, sizeof(int) * ns));
     TG_CUDA(cudaMalloc(&b->d_sh_nprim, sizeof(int) * ns));
@@ -125,15 +144,29 @@ int basis_setup(tg_basis *b, const double *xyz, const double *exps, const double
     std::vector<int2> prs((size_t)npr);
     for (int x = 0; x < ns; ++x)
         for (int y = 0; y <= x; ++y) prs[(size_t)pkey(x, y)] = make_int2(x, y);
+    std::vector<long long> bpoff((size_t)npr + 1);
+    {
+        long long o = 0;
+        for (long long k = 0; k < npr; ++k) {
+            bpoff[(size_t)k] = o;
+            o += (long long)b->sh_nprim[prs[(size_t)k].x] * b->sh_nprim[prs[(size_t)k].y];
+        }
+        bpoff[(size_t)npr] = o;
+    }
     int2 *d_prs = nullptr;
     double *d_Q = nullptr, *d_Qd = nullptr;
     cudaError_t e = cudaMalloc(&d_prs, sizeof(int2) * npr);
     if (e == cudaSuccess) e = cudaMalloc(&d_Q, sizeof(double) * npr);
     if (e == cudaSuccess) e = cudaMalloc(&d_Qd, sizeof(double) * npr);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bpoff, sizeof(long long) * (npr + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bp, sizeof(double) * std::max<long long>(bpoff[(size_t)npr], 1));
     if (e == cudaSuccess) e = cudaMemcpy(d_prs, prs.data(), sizeof(int2) * npr, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_bpoff, bpoff.data(), sizeof(long long) * (npr + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_schwarz<<<(unsigned)((npr + 127) / 128), 128>>>((int)npr, d_prs, b->d_xyz, b->d_sh_atom, b->d_sh_l,
-                                                          b->d_sh_nprim, b->d_sh_poff, b->d_exps, b->d_cn, d_Q, d_Qd);
+                                                          b->d_sh_nprim, b->d_sh_poff, b->d_exps, b->d_cn, d_Q, d_Qd,
+                                                          b->d_bpoff, b->d_bp);
         e = cudaGetLastError();
     }
     b->Q.resize((size_t)npr);
@@ -158,6 +191,10 @@ struct HostPair {
     int sa, sb, np, key;
     double Q, Qd;
 };
+
+// fp32 relative error assumed by the bound router, per quartet, relative to
+// nfq * bound (see tg_grad2e)
+constexpr double kEps32Bound = 3e-6;
 
 }  // namespace
 
@@ -251,24 +288,66 @@ void tg_basis_destroy(tg_basis *b)
     delete b;
 }
 
-int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_options *opt_in, double *grad,
-              tg_stats *stats)
+}  // extern "C"
+
+namespace {
+
+struct HostTile {
+    unsigned bt, kt;
+    long long cost;
+    double bnd;  // rigorous bound of any per-function-quartet contribution in the tile
+    int qc;
+};
+
+// Host plan of one call: device densities and block factors, screened and
+// sorted shell pairs, primitive-pair records, and the unrouted tile list.
+struct Plan {
+    int npair = 0;
+    DensArgs den;
+    GeoArgs geo;
+    ScreenArgs scr;
+    PrimPairs pp;
+    double tau = 0.0, scale = 0.0;
+    double *dM = nullptr, *dMrow = nullptr, *dgrad = nullptr;
+    unsigned long long *dcnt = nullptr;
+    std::vector<double> Mrow;
+    std::vector<HostPair> cls[NPC];
+    int cls_off[NPC + 1];
+    long long npairs_kept = 0, nprimpairs = 0;
+    int *d_sa = nullptr, *d_sb = nullptr, *d_poff = nullptr, *d_np = nullptr, *d_key = nullptr;
+    double *d_Q = nullptr, *d_Qd = nullptr;
+    std::vector<HostTile> tiles;
+    int qc_P[NQC], qc_Q[NQC];
+    int launches = 0;
+    int G = 1;
+    PairSet set(int c) const
+    {
+        PairSet s;
+        const int o = cls_off[c];
+        s.n = (int)cls[c].size();
+        s.sa = d_sa + o;
+        s.sb = d_sb + o;
+        s.poff = d_poff + o;
+        s.np = d_np + o;
+        s.Q = d_Q + o;
+        s.Qd = d_Qd + o;
+        s.key = d_key + o;
+        return s;
+    }
+};
+
+int check_pairs(int npair, const tg_pair *pairs, const tg_options &opt, double &omega, int &use_lr)
 {
-    auto t0 = std::chrono::steady_clock::now();
-    tg_basis *b = const_cast<tg_basis *>(cb);
-    if (!b || !pairs || !grad) return TG_EINVAL;
-    tg_options opt;
-    if (opt_in) opt = *opt_in;
-    else tg_options_default(&opt);
-    if (npair < 1) return TG_EINVAL;
+    if (npair < 1 || !pairs) return TG_EINVAL;
     if (npair > TG_MAX_PAIRS) return TG_EUNSUPPORTED;
     if (!(opt.screen_tol >= 0.0) || !std::isfinite(opt.screen_tol)) return TG_EINVAL;
     if (opt.nranks < 1 || opt.rank < 0 || opt.rank >= opt.nranks) return TG_EINVAL;
-    if (opt.precision != TG_FP64 && opt.precision != TG_MIXED_BOUND && opt.precision != TG_MIXED_LEARNED)
+    if (opt.precision != TG_FP64 && opt.precision != TG_MIXED_BOUND && opt.precision != TG_MIXED_LEARNED &&
+        opt.precision != TG_FP32)
         return TG_EINVAL;
-    if (opt.precision != TG_FP64) return TG_EUNSUPPORTED;
-    double omega = 0.0;
-    int use_lr = 0;
+    if (!(opt.mixed_tol >= 0.0) || !std::isfinite(opt.mixed_tol)) return TG_EINVAL;
+    omega = 0.0;
+    use_lr = 0;
     for (int p = 0; p < npair; ++p) {
         const tg_pair &q = pairs[p];
         if (!q.A || !q.B) return TG_EINVAL;
@@ -280,20 +359,22 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
             omega = q.omega;
         }
     }
-    cudaStream_t st = (cudaStream_t)opt.stream;
+    return TG_OK;
+}
+
+// Densities, block factors, screened pairs, primitive pairs, unrouted tiles.
+int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &opt, cudaStream_t st, Plan &pl)
+{
+    double omega;
+    int use_lr;
+    int rc = check_pairs(npair, pairs, opt, omega, use_lr);
+    if (rc != TG_OK) return rc;
     const int nbf = b->nbf, ns = b->nshell, natom = b->natom;
     const size_t nbf2 = (size_t)nbf * nbf;
     TG_CUDA(cudaSetDevice(b->device));
-
-    // ---- pass 1: densities, symmetrised copies, block maxima
-    DevArena &W = b->ws;
-    const int nmat_up = opt.device_ptrs ? 0 : 2 * npair;
-    size_t need1 = al(sizeof(double) * nbf2) * (nmat_up + 2 * npair) + al(sizeof(double) * (size_t)ns * ns) +
-                   al(sizeof(double) * ns) + al(sizeof(double) * TG_MAX_PAIRS) + al(sizeof(double) * 3 * natom) +
-                   al(sizeof(unsigned long long) * 3 * NQC) + 4096;
-    // pass-2 sizes are not known yet; reserve pass 1 now and grow below
-    DensArgs den;
-    std::memset(&den, 0, sizeof(den));
+    pl.npair = npair;
+    std::memset(&pl.den, 0, sizeof(pl.den));
+    DensArgs &den = pl.den;
     den.npair = npair;
     den.nbf = nbf;
     den.use_lr = use_lr;
@@ -303,25 +384,22 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
         den.cK[p] = pairs[p].c_K;
         den.cKlr[p] = (pairs[p].omega > 0.0) ? pairs[p].c_K_lr : 0.0;
     }
-
-    // ---- host pair screening needs Mmax; compute it after upload.  To keep
-    // one arena, the arena is sized for pass 1 plus the largest possible pass 2
-    // (all candidate pairs kept) on first use.
-    const long long npr_all = (long long)ns * (ns + 1) / 2;
-
-    W.used = 0;
+    // ---- arena 1: densities, symmetrised copies, block factors, output
+    DevArena &W = b->ws1;
+    const int nmat_up = opt.device_ptrs ? 0 : 2 * npair;
+    const size_t need1 = al(sizeof(double) * nbf2) * (nmat_up + 2 * npair) + al(sizeof(double) * (size_t)ns * ns) +
+                         al(sizeof(double) * ns) + al(sizeof(double) * TG_MAX_PAIRS) +
+                         al(sizeof(double) * 3 * natom) + al(sizeof(unsigned long long) * 3 * NQC) + 4096;
     TG_CUDA(W.reserve(need1));
-    double *dmat[2 * TG_MAX_PAIRS];
+    W.used = 0;
+    double *dmat[2 * TG_MAX_PAIRS], *dS[2 * TG_MAX_PAIRS];
     for (int k = 0; k < nmat_up; ++k) dmat[k] = W.take<double>(nbf2);
-    double *dS[2 * TG_MAX_PAIRS];
     for (int k = 0; k < 2 * npair; ++k) dS[k] = W.take<double>(nbf2);
-    double *dM = W.take<double>((size_t)ns * ns);
-    double *dMrow = W.take<double>(ns);
+    pl.dM = W.take<double>((size_t)ns * ns);
+    pl.dMrow = W.take<double>(ns);
     double *dw = W.take<double>(TG_MAX_PAIRS);
-    double *dgrad = W.take<double>(3 * natom);
-    unsigned long long *dcnt = W.take<unsigned long long>(3 * NQC);
-    const size_t pass1_used = W.used;
-
+    pl.dgrad = W.take<double>(3 * natom);
+    pl.dcnt = W.take<unsigned long long>(3 * NQC);
     for (int p = 0; p < npair; ++p) {
         if (opt.device_ptrs) {
             den.A[p] = pairs[p].A;
@@ -337,26 +415,28 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
         k_symm<<<gs, 256, 0, st>>>(nbf, den.B[p], dS[2 * p + 1]);
         den.S[p] = dS[2 * p];
         den.T[p] = dS[2 * p + 1];
+        pl.launches += 2;
     }
     double hw[TG_MAX_PAIRS];
-    for (int p = 0; p < npair; ++p) hw[p] = std::sqrt(std::fabs(den.cJ[p]) + std::fabs(den.cK[p]) + std::fabs(den.cKlr[p]));
+    for (int p = 0; p < npair; ++p)
+        hw[p] = std::sqrt(std::fabs(den.cJ[p]) + std::fabs(den.cK[p]) + std::fabs(den.cKlr[p]));
     TG_CUDA(cudaMemcpyAsync(dw, hw, sizeof(double) * npair, cudaMemcpyHostToDevice, st));
-    {
-        const unsigned gs = (unsigned)((npr_all + 127) / 128);
-        k_blockmax<<<gs, 128, 0, st>>>(ns, b->d_sh_bf, b->d_sh_l, den, dw, dM, dMrow);
-        k_rowmax<<<(ns + 127) / 128, 128, 0, st>>>(ns, dM, dMrow);
-        TG_CUDA(cudaGetLastError());
-    }
-    std::vector<double> Mrow(ns);
-    TG_CUDA(cudaMemcpyAsync(Mrow.data(), dMrow, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    const long long npr_all = (long long)ns * (ns + 1) / 2;
+    k_blockmax<<<(unsigned)((npr_all + 127) / 128), 128, 0, st>>>(ns, b->d_sh_bf, b->d_sh_l, den, dw, pl.dM,
+                                                                   pl.dMrow);
+    k_rowmax<<<(ns + 127) / 128, 128, 0, st>>>(ns, pl.dM, pl.dMrow);
+    pl.launches += 2;
+    TG_CUDA(cudaGetLastError());
+    pl.Mrow.resize(ns);
+    TG_CUDA(cudaMemcpyAsync(pl.Mrow.data(), pl.dMrow, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
     TG_CUDA(cudaStreamSynchronize(st));
     double Mmax = 0.0;
-    for (int x = 0; x < ns; ++x) Mmax = std::max(Mmax, Mrow[x]);
+    for (int x = 0; x < ns; ++x) Mmax = std::max(Mmax, pl.Mrow[x]);
 
-    // ---- pair screening and class sort (Sec. II.C: presort by K and Schwarz bound)
-    const double tau = opt.screen_tol;
-    const double scale = 8.0 * npair;
-    std::vector<HostPair> cls[NPC];
+    // ---- pair screening and class sort (Sec. II.C: presort by K and the Schwarz bound)
+    pl.tau = opt.screen_tol;
+    pl.scale = 8.0 * npair;
+    const double tau = pl.tau, scale = pl.scale;
     for (int x = 0; x < ns; ++x)
         for (int y = 0; y <= x; ++y) {
             const long long k = pkey(x, y);
@@ -374,28 +454,84 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
             hp.key = (int)k;
             hp.Q = q;
             hp.Qd = qd;
-            cls[pair_class(b->sh_l[sa], b->sh_l[sb])].push_back(hp);
+            pl.cls[pair_class(b->sh_l[sa], b->sh_l[sb])].push_back(hp);
         }
-    long long npairs_kept = 0, nprimpairs = 0;
+    // surviving primitive pairs per kept shell pair (primitive screen, see tdgrad.h)
+    const double eps_p = tau > 0.0 ? 1e-6 * tau : 0.0;
+    const double qq = std::max(b->Qmax, b->Qdmax);
+    long long nk_all = 0, npp_max = 0;
     for (int c = 0; c < NPC; ++c) {
-        std::sort(cls[c].begin(), cls[c].end(), [](const HostPair &u, const HostPair &v) {
-            if (u.np != v.np) return u.np > v.np;
-            if (u.Qd != v.Qd) return u.Qd > v.Qd;
-            return u.key < v.key;
-        });
-        npairs_kept += (long long)cls[c].size();
-        for (auto &hp : cls[c]) nprimpairs += hp.np;
+        nk_all += (long long)pl.cls[c].size();
+        for (auto &hp : pl.cls[c]) npp_max += hp.np;
     }
-    // per-tile-block maxima for the tile bounds
+    // ---- arena 2: pair arrays, primitive-pair records, tiles, features, partials
+    pl.G = std::max(1, 2 * b->nsm);
+    {
+        const size_t np_k = (size_t)std::max<long long>(nk_all, 1);
+        const size_t npp = (size_t)std::max<long long>(npp_max, 1);
+        // tiles: at most one per (bra tile, ket tile) combination of every class
+        long long ntl_max = 0;
+        for (int P = 0; P < NPC; ++P)
+            for (int Qc = 0; Qc <= P; ++Qc)
+                ntl_max += (long long)((pl.cls[P].size() + TB - 1) / TB) * ((pl.cls[Qc].size() + TK - 1) / TK);
+        const size_t ntl = (size_t)std::max<long long>(ntl_max, 1);
+        const size_t need2 = 6 * al(sizeof(int) * np_k) + 2 * al(sizeof(double) * np_k) +
+                             6 * al(sizeof(double) * npp) + 6 * al(sizeof(float) * npp) + al(sizeof(uint2) * ntl) +
+                             al(sizeof(TileRef) * ntl) + al(sizeof(float) * ntl * (NFEAT + 1)) +
+                             al(sizeof(double) * (size_t)pl.G * 3 * natom) + 8192;
+        DevArena &V = b->ws2;
+        TG_CUDA(V.reserve(need2));
+        V.used = 0;
+        pl.d_sa = V.take<int>(np_k);
+        pl.d_sb = V.take<int>(np_k);
+        pl.d_poff = V.take<int>(np_k);
+        pl.d_np = V.take<int>(np_k);
+        pl.d_key = V.take<int>(np_k);
+        pl.d_Q = V.take<double>(np_k);
+        pl.d_Qd = V.take<double>(np_k);
+        int *d_cnt = V.take<int>(np_k);
+        std::vector<int> u_sa, u_sb, u_key;
+        for (int c = 0; c < NPC; ++c)
+            for (auto &hp : pl.cls[c]) {
+                u_sa.push_back(hp.sa);
+                u_sb.push_back(hp.sb);
+                u_key.push_back(hp.key);
+            }
+        if (nk_all > 0) {
+            TG_CUDA(cudaMemcpyAsync(pl.d_sa, u_sa.data(), sizeof(int) * nk_all, cudaMemcpyHostToDevice, st));
+            TG_CUDA(cudaMemcpyAsync(pl.d_sb, u_sb.data(), sizeof(int) * nk_all, cudaMemcpyHostToDevice, st));
+            TG_CUDA(cudaMemcpyAsync(pl.d_key, u_key.data(), sizeof(int) * nk_all, cudaMemcpyHostToDevice, st));
+            k_prim_count<<<(unsigned)((nk_all + 127) / 128), 128, 0, st>>>((int)nk_all, pl.d_sa, pl.d_sb, pl.d_key,
+                                                                           b->d_sh_nprim, b->d_bpoff, b->d_bp, scale,
+                                                                           qq, Mmax, eps_p, d_cnt);
+            ++pl.launches;
+            TG_CUDA(cudaGetLastError());
+            std::vector<int> cnt((size_t)nk_all);
+            TG_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * nk_all, cudaMemcpyDeviceToHost, st));
+            TG_CUDA(cudaStreamSynchronize(st));
+            size_t i = 0;
+            for (int c = 0; c < NPC; ++c) {
+                std::vector<HostPair> kept;
+                for (auto &hp : pl.cls[c]) {
+                    hp.np = cnt[i++];
+                    if (hp.np > 0) kept.push_back(hp);
+                }
+                pl.cls[c].swap(kept);
+            }
+        }
+    }
     std::vector<int> h_sa, h_sb, h_poff, h_np, h_key;
     std::vector<double> h_Q, h_Qd;
-    h_sa.reserve(npairs_kept);
-    int cls_off[NPC + 1];
     {
         int po = 0, n = 0;
         for (int c = 0; c < NPC; ++c) {
-            cls_off[c] = n;
-            for (auto &hp : cls[c]) {
+            std::sort(pl.cls[c].begin(), pl.cls[c].end(), [](const HostPair &u, const HostPair &v) {
+                if (u.np != v.np) return u.np > v.np;
+                if (u.Qd != v.Qd) return u.Qd > v.Qd;
+                return u.key < v.key;
+            });
+            pl.cls_off[c] = n;
+            for (auto &hp : pl.cls[c]) {
                 h_sa.push_back(hp.sa);
                 h_sb.push_back(hp.sb);
                 h_poff.push_back(po);
@@ -407,208 +543,312 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
                 ++n;
             }
         }
-        cls_off[NPC] = n;
+        pl.cls_off[NPC] = n;
+        pl.npairs_kept = n;
+        pl.nprimpairs = po;
     }
 
-    // ---- quartet tiles per class, screened by a tile bound, sorted by cost
-    struct HostTile {
-        unsigned bt, kt;
-        long long cost;
-    };
-    std::vector<uint2> tiles_all;
-    long long tile_off[NQC + 1];
-    int qc_P[NQC], qc_Q[NQC];
+    // ---- unrouted quartet tiles with their bounds (screened)
     for (int P = 0; P < NPC; ++P)
         for (int Qc = 0; Qc <= P; ++Qc) {
-            qc_P[P * (P + 1) / 2 + Qc] = P;
-            qc_Q[P * (P + 1) / 2 + Qc] = Qc;
+            pl.qc_P[P * (P + 1) / 2 + Qc] = P;
+            pl.qc_Q[P * (P + 1) / 2 + Qc] = Qc;
         }
     auto blockmax = [&](int c, int blk, int bsz, double &q, double &qd, double &m) {
         q = qd = m = 0.0;
-        const int lo = blk * bsz, hi = std::min((int)cls[c].size(), lo + bsz);
+        const int lo = blk * bsz, hi = std::min((int)pl.cls[c].size(), lo + bsz);
         for (int i = lo; i < hi; ++i) {
-            const HostPair &hp = cls[c][i];
+            const HostPair &hp = pl.cls[c][i];
             q = std::max(q, hp.Q);
             qd = std::max(qd, hp.Qd);
-            m = std::max(m, std::max(Mrow[hp.sa], Mrow[hp.sb]));
+            m = std::max(m, std::max(pl.Mrow[hp.sa], pl.Mrow[hp.sb]));
         }
     };
     for (int qc = 0; qc < NQC; ++qc) {
-        tile_off[qc] = (long long)tiles_all.size();
-        const int P = qc_P[qc], Qc = qc_Q[qc];
-        const int nP = (int)cls[P].size(), nQ = (int)cls[Qc].size();
+        const int P = pl.qc_P[qc], Qc = pl.qc_Q[qc];
+        const int nP = (int)pl.cls[P].size(), nQ = (int)pl.cls[Qc].size();
         if (!nP || !nQ) continue;
         const int nbt = (nP + TB - 1) / TB, nkt = (nQ + TK - 1) / TK;
         std::vector<double> bq(nbt), bqd(nbt), bm(nbt), kq(nkt), kqd(nkt), km(nkt);
         for (int i = 0; i < nbt; ++i) blockmax(P, i, TB, bq[i], bqd[i], bm[i]);
         for (int i = 0; i < nkt; ++i) blockmax(Qc, i, TK, kq[i], kqd[i], km[i]);
-        std::vector<HostTile> ts;
         for (int bt = 0; bt < nbt; ++bt)
             for (int kt = 0; kt < nkt; ++kt) {
                 if (P == Qc && kt * TK > bt * TB + TB - 1) continue;
-                if (tau > 0.0) {
-                    const double Mt = std::max(bm[bt], km[kt]);
-                    const double bnd = scale * std::max(bqd[bt] * kq[kt], bq[bt] * kqd[kt]) * Mt * Mt;
-                    if (bnd < tau) continue;
-                }
+                const double Mt = std::max(bm[bt], km[kt]);
+                const double bnd = scale * std::max(bqd[bt] * kq[kt], bq[bt] * kqd[kt]) * Mt * Mt;
+                if (tau > 0.0 && bnd < tau) continue;
                 HostTile t;
                 t.bt = bt;
                 t.kt = kt;
-                t.cost = (long long)cls[P][bt * TB].np * cls[Qc][kt * TK].np;
-                ts.push_back(t);
+                t.cost = (long long)pl.cls[P][bt * TB].np * pl.cls[Qc][kt * TK].np;
+                t.bnd = bnd;
+                t.qc = qc;
+                pl.tiles.push_back(t);
             }
-        std::stable_sort(ts.begin(), ts.end(), [](const HostTile &u, const HostTile &v) { return u.cost > v.cost; });
-        for (auto &t : ts) tiles_all.push_back(make_uint2(t.bt, t.kt));
     }
-    tile_off[NQC] = (long long)tiles_all.size();
 
-    // ---- pass 2 buffers
-    const int G = std::max(1, 2 * b->nsm);
-    const size_t np_k = (size_t)std::max<long long>(npairs_kept, 1);
-    const size_t npp = (size_t)std::max<long long>(nprimpairs, 1);
-    size_t need2 = pass1_used + 5 * al(sizeof(int) * np_k) + 2 * al(sizeof(double) * np_k) +
-                   6 * al(sizeof(double) * npp) + 6 * al(sizeof(float) * npp) +
-                   al(sizeof(uint2) * std::max<size_t>(tiles_all.size(), 1)) + al(sizeof(double) * (size_t)G * 3 * natom) +
-                   4096;
-    if (need2 > W.cap) {
-        // grow and redo pass 1 in the bigger arena (the device copies are cheap)
-        TG_CUDA(cudaStreamSynchronize(st));
-        W.release();
-        TG_CUDA(W.reserve(need2 + need2 / 4));
-        return tg_grad2e(cb, npair, pairs, opt_in, grad, stats);
-    }
-    int *d_sa = W.take<int>(np_k), *d_sb = W.take<int>(np_k), *d_poff = W.take<int>(np_k), *d_np = W.take<int>(np_k),
-        *d_key = W.take<int>(np_k);
-    double *d_Q = W.take<double>(np_k), *d_Qd = W.take<double>(np_k);
-    double *pp_p = W.take<double>(npp), *pp_x = W.take<double>(npp), *pp_y = W.take<double>(npp),
-           *pp_z = W.take<double>(npp), *pp_K = W.take<double>(npp), *pp_za = W.take<double>(npp);
-    float *fp_p = W.take<float>(npp), *fp_x = W.take<float>(npp), *fp_y = W.take<float>(npp),
-          *fp_z = W.take<float>(npp), *fp_K = W.take<float>(npp), *fp_za = W.take<float>(npp);
-    uint2 *d_tiles = W.take<uint2>(std::max<size_t>(tiles_all.size(), 1));
-    double *d_part = W.take<double>((size_t)G * 3 * natom);
-
-    if (npairs_kept > 0) {
-        TG_CUDA(cudaMemcpyAsync(d_sa, h_sa.data(), sizeof(int) * npairs_kept, cudaMemcpyHostToDevice, st));
-        TG_CUDA(cudaMemcpyAsync(d_sb, h_sb.data(), sizeof(int) * npairs_kept, cudaMemcpyHostToDevice, st));
-        TG_CUDA(cudaMemcpyAsync(d_poff, h_poff.data(), sizeof(int) * npairs_kept, cudaMemcpyHostToDevice, st));
-        TG_CUDA(cudaMemcpyAsync(d_np, h_np.data(), sizeof(int) * npairs_kept, cudaMemcpyHostToDevice, st));
-        TG_CUDA(cudaMemcpyAsync(d_key, h_key.data(), sizeof(int) * npairs_kept, cudaMemcpyHostToDevice, st));
-        TG_CUDA(cudaMemcpyAsync(d_Q, h_Q.data(), sizeof(double) * npairs_kept, cudaMemcpyHostToDevice, st));
-        TG_CUDA(cudaMemcpyAsync(d_Qd, h_Qd.data(), sizeof(double) * npairs_kept, cudaMemcpyHostToDevice, st));
-        k_prim_pairs<<<(unsigned)((npairs_kept + 127) / 128), 128, 0, st>>>(
-            (int)npairs_kept, d_sa, d_sb, d_poff, b->d_xyz, b->d_sh_atom, b->d_sh_nprim, b->d_sh_poff, b->d_exps,
-            b->d_cn, pp_p, pp_x, pp_y, pp_z, pp_K, pp_za, fp_p, fp_x, fp_y, fp_z, fp_K, fp_za);
+    DevArena &V = b->ws2;
+    const size_t npp = (size_t)std::max<long long>(pl.nprimpairs, 1);
+    double *pp_p = V.take<double>(npp), *pp_x = V.take<double>(npp), *pp_y = V.take<double>(npp),
+           *pp_z = V.take<double>(npp), *pp_K = V.take<double>(npp), *pp_za = V.take<double>(npp);
+    float *fp_p = V.take<float>(npp), *fp_x = V.take<float>(npp), *fp_y = V.take<float>(npp),
+          *fp_z = V.take<float>(npp), *fp_K = V.take<float>(npp), *fp_za = V.take<float>(npp);
+    const long long nk = pl.npairs_kept;
+    if (nk > 0) {
+        TG_CUDA(cudaMemcpyAsync(pl.d_sa, h_sa.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(pl.d_sb, h_sb.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(pl.d_poff, h_poff.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(pl.d_np, h_np.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(pl.d_key, h_key.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(pl.d_Q, h_Q.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(pl.d_Qd, h_Qd.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+        k_prim_pairs<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(
+            (int)nk, pl.d_sa, pl.d_sb, pl.d_poff, pl.d_key, b->d_xyz, b->d_sh_atom, b->d_sh_nprim, b->d_sh_poff,
+            b->d_exps, b->d_cn, b->d_bpoff, b->d_bp, scale, qq, Mmax, eps_p, pp_p, pp_x, pp_y, pp_z, pp_K, pp_za, fp_p,
+            fp_x, fp_y, fp_z, fp_K, fp_za);
+        ++pl.launches;
         TG_CUDA(cudaGetLastError());
+        // the host pair vectors must outlive the asynchronous copies
+        TG_CUDA(cudaStreamSynchronize(st));
     }
-    if (!tiles_all.empty())
-        TG_CUDA(cudaMemcpyAsync(d_tiles, tiles_all.data(), sizeof(uint2) * tiles_all.size(), cudaMemcpyHostToDevice, st));
-    TG_CUDA(cudaMemsetAsync(d_part, 0, sizeof(double) * (size_t)G * 3 * natom, st));
-    TG_CUDA(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * 3 * NQC, st));
+    pl.pp.p = pp_p;
+    pl.pp.Px = pp_x;
+    pl.pp.Py = pp_y;
+    pl.pp.Pz = pp_z;
+    pl.pp.K = pp_K;
+    pl.pp.za = pp_za;
+    pl.pp.fp = fp_p;
+    pl.pp.fPx = fp_x;
+    pl.pp.fPy = fp_y;
+    pl.pp.fPz = fp_z;
+    pl.pp.fK = fp_K;
+    pl.pp.fza = fp_za;
+    pl.geo.natom = natom;
+    pl.geo.nshell = ns;
+    pl.geo.xyz = b->d_xyz;
+    pl.geo.sh_atom = b->d_sh_atom;
+    pl.geo.sh_bf = b->d_sh_bf;
+    pl.scr.tau = tau;
+    pl.scr.scale = scale;
+    pl.scr.M = pl.dM;
+    pl.scr.nshell = ns;
+    pl.scr.rank = opt.rank;
+    pl.scr.nranks = opt.nranks;
+    return TG_OK;
+}
 
-    GeoArgs geo;
-    geo.natom = natom;
-    geo.nshell = ns;
-    geo.xyz = b->d_xyz;
-    geo.sh_atom = b->d_sh_atom;
-    geo.sh_bf = b->d_sh_bf;
-    ScreenArgs scr;
-    scr.tau = tau;
-    scr.scale = scale;
-    scr.M = dM;
-    scr.nshell = ns;
-    scr.rank = opt.rank;
-    scr.nranks = opt.nranks;
-    PrimPairs pp;
-    pp.p = pp_p;
-    pp.Px = pp_x;
-    pp.Py = pp_y;
-    pp.Pz = pp_z;
-    pp.K = pp_K;
-    pp.za = pp_za;
-    pp.fp = fp_p;
-    pp.fPx = fp_x;
-    pp.fPy = fp_y;
-    pp.fPz = fp_z;
-    pp.fK = fp_K;
-    pp.fza = fp_za;
+FeatureArgs feature_args(const tg_basis *b, const Plan &pl)
+{
+    FeatureArgs fa;
+    for (int c = 0; c < NPC; ++c) fa.sets[c] = pl.set(c);
+    fa.M = pl.dM;
+    fa.xyz = b->d_xyz;
+    fa.sh_atom = b->d_sh_atom;
+    fa.pp_p = pl.pp.p;
+    fa.nshell = b->nshell;
+    fa.scale = pl.scale;
+    return fa;
+}
+
+// Features and router predictions (log10 magnitude) for the listed tiles.
+int predict_tiles(tg_basis *b, const Plan &pl, const tg_router *r, const std::vector<size_t> &idx, cudaStream_t st,
+                  TileRef *d_ref, float *d_feat, float *d_pred, std::vector<float> *pred, std::vector<float> *feat,
+                  int &launches)
+{
+    const size_t n = idx.size();
+    if (!n) return TG_OK;
+    std::vector<TileRef> refs(n);
+    for (size_t i = 0; i < n; ++i) {
+        const HostTile &t = pl.tiles[idx[i]];
+        refs[i].P = pl.qc_P[t.qc];
+        refs[i].Q = pl.qc_Q[t.qc];
+        refs[i].bt = t.bt;
+        refs[i].kt = t.kt;
+    }
+    TG_CUDA(cudaMemcpyAsync(d_ref, refs.data(), sizeof(TileRef) * n, cudaMemcpyHostToDevice, st));
+    k_tile_features<<<(unsigned)((n + 127) / 128), 128, 0, st>>>((int)n, d_ref, feature_args(b, pl), d_feat);
+    ++launches;
+    TG_CUDA(cudaGetLastError());
+    if (r) {
+        float *dparams = b->d_router;
+        TG_CUDA(cudaMemcpyAsync(dparams, r->params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(dparams + NPARAM, r->mu, sizeof(float) * NFEAT, cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemcpyAsync(dparams + NPARAM + NFEAT, r->sd, sizeof(float) * NFEAT, cudaMemcpyHostToDevice, st));
+        k_mlp_predict<<<(unsigned)((n + 127) / 128), 128, 0, st>>>((int)n, d_feat, dparams + NPARAM,
+                                                                    dparams + NPARAM + NFEAT, dparams, d_pred);
+        ++launches;
+        TG_CUDA(cudaGetLastError());
+        if (pred) {
+            pred->resize(n);
+            TG_CUDA(cudaMemcpyAsync(pred->data(), d_pred, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    if (feat) {
+        feat->resize(n * NFEAT);
+        TG_CUDA(cudaMemcpyAsync(feat->data(), d_feat, sizeof(float) * n * NFEAT, cudaMemcpyDeviceToHost, st));
+    }
+    TG_CUDA(cudaStreamSynchronize(st));
+    return TG_OK;
+}
+
+// Launch the class kernels over per-(class, precision) tile lists.  With
+// dump != nullptr every quartet's 12 gradient components are written to
+// dump[(list position * TILE + thread) * 12 + k] instead of being reduced.
+int launch_lists(tg_basis *b, Plan &pl, const std::vector<std::vector<size_t>> &lists, uint2 *d_tiles,
+                 double *d_part, double *dump, bool timing, cudaStream_t st, tg_stats *stats, int &launches)
+{
+    std::vector<uint2> flat;
+    std::vector<long long> off(2 * NQC + 1);
+    for (int k = 0; k < 2 * NQC; ++k) {
+        off[k] = (long long)flat.size();
+        for (size_t i : lists[k]) flat.push_back(make_uint2(pl.tiles[i].bt, pl.tiles[i].kt));
+    }
+    off[2 * NQC] = (long long)flat.size();
+    if (!flat.empty())
+        TG_CUDA(cudaMemcpyAsync(d_tiles, flat.data(), sizeof(uint2) * flat.size(), cudaMemcpyHostToDevice, st));
+    const int natom = b->natom;
     OutArgs out;
     out.partials = d_part;
-    out.counters = dcnt;
+    out.dump = dump;
     const size_t stage = (size_t)TILE * 12 * sizeof(double) + (size_t)TILE * 4 * sizeof(int);
     const size_t sgrad = (size_t)3 * natom * sizeof(double);
     out.use_smem = (stage + sgrad) <= 160 * 1024;
     const size_t smem = stage + (out.use_smem ? sgrad : 0);
-
-    auto mkset = [&](int c) {
-        PairSet s;
-        const int o = cls_off[c];
-        s.n = (int)cls[c].size();
-        s.sa = d_sa + o;
-        s.sb = d_sb + o;
-        s.poff = d_poff + o;
-        s.np = d_np + o;
-        s.Q = d_Q + o;
-        s.Qd = d_Qd + o;
-        s.key = d_key + o;
-        return s;
-    };
-    int launches = 2 * npair + 3 + (npairs_kept > 0 ? 1 : 0);
-    cudaEvent_t ev[NQC + 1];
-    bool timed[NQC];
-    const bool timing = opt.timing != 0;
-    for (int qc = 0; qc < NQC; ++qc) timed[qc] = false;
-    if (timing)
-        for (int k = 0; k <= NQC; ++k) TG_CUDA(cudaEventCreate(&ev[k]));
-    for (int qc = 0; qc < NQC; ++qc) {
-        const long long nt = tile_off[qc + 1] - tile_off[qc];
-        if (nt <= 0) continue;
-        ClassLaunch cl;
-        cl.bra = mkset(qc_P[qc]);
-        cl.ket = mkset(qc_Q[qc]);
-        cl.same = qc_P[qc] == qc_Q[qc];
-        cl.ntiles = nt;
-        cl.tiles = d_tiles + tile_off[qc];
-        cl.route = nullptr;
-        OutArgs o = out;
-        o.counters = dcnt + 3 * qc;
-        const int grid = (int)std::min<long long>(nt, G);
-        if (timing) cudaEventRecord(ev[qc], st);
-        cudaError_t e = kClassLaunchers[qc](0, grid, smem, st, geo, den, scr, cl, o, pp, b->d_boys);
-        if (timing) {
-            cudaEventRecord(ev[NQC], st);
-            cudaEventSynchronize(ev[NQC]);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[qc], ev[NQC]);
-            if (stats) stats->class_ms[qc] = ms;
-            timed[qc] = true;
-        }
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            if (timing)
-                for (int k = 0; k <= NQC; ++k) cudaEventDestroy(ev[k]);
-            return TG_ECUDA;
-        }
-        ++launches;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timing) {
+        TG_CUDA(cudaEventCreate(&e0));
+        TG_CUDA(cudaEventCreate(&e1));
     }
-    if (timing)
-        for (int k = 0; k <= NQC; ++k) cudaEventDestroy(ev[k]);
-    k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, G, d_part, dgrad);
+    int rc = TG_OK;
+    for (int qc = 0; qc < NQC && rc == TG_OK; ++qc) {
+        bool any = false;
+        for (int r = 0; r < 2; ++r) {
+            const long long nt = off[2 * qc + r + 1] - off[2 * qc + r];
+            if (nt <= 0) continue;
+            ClassLaunch cl;
+            cl.bra = pl.set(pl.qc_P[qc]);
+            cl.ket = pl.set(pl.qc_Q[qc]);
+            cl.same = pl.qc_P[qc] == pl.qc_Q[qc];
+            cl.ntiles = nt;
+            cl.tiles = d_tiles + off[2 * qc + r];
+            cl.route = nullptr;
+            OutArgs o = out;
+            o.counters = pl.dcnt + 3 * qc;
+            if (dump) o.dump = dump + (size_t)off[2 * qc + r] * TILE * 12;
+            const int grid = (int)std::min<long long>(nt, pl.G);
+            if (timing && !any) cudaEventRecord(e0, st);
+            cudaError_t e =
+                kClassLaunchers[qc](r, grid, smem, st, pl.geo, pl.den, pl.scr, cl, o, pl.pp, b->d_boys);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                rc = TG_ECUDA;
+                break;
+            }
+            any = true;
+            ++launches;
+        }
+        if (timing && any && rc == TG_OK) {
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (stats) stats->class_ms[qc] = ms;
+        }
+    }
+    if (timing) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_options *opt_in, double *grad,
+              tg_stats *stats)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    tg_basis *b = const_cast<tg_basis *>(cb);
+    if (!b || !pairs || !grad) return TG_EINVAL;
+    tg_options opt;
+    if (opt_in) opt = *opt_in;
+    else tg_options_default(&opt);
+    if (opt.precision == TG_MIXED_LEARNED && (!opt.router || !opt.router->trained)) return TG_EROUTER;
+    cudaStream_t st = (cudaStream_t)opt.stream;
+    Plan pl;
+    int rc = make_plan(b, npair, pairs, opt, st, pl);
+    if (rc != TG_OK) return rc;
+    const int natom = b->natom;
+    int launches = pl.launches;
+
+    // ---- routing: fp32 for the tiles with the smallest error estimate while
+    // the summed estimate stays within mixed_tol.  Estimates: every gradient
+    // component of a quartet is at most nfq * bound (bound router) or
+    // 10^(prediction + margin) (learned router); fp32 errs by eps_rel of that.
+    const size_t ntl = pl.tiles.size();
+    std::vector<uint8_t> route(ntl, 0);
+    DevArena &V = b->ws2;
+    uint2 *d_tiles = V.take<uint2>(std::max<size_t>(ntl, 1));
+    TileRef *d_ref = V.take<TileRef>(std::max<size_t>(ntl, 1));
+    float *d_feat = V.take<float>(std::max<size_t>(ntl, 1) * NFEAT);
+    float *d_pred = V.take<float>(std::max<size_t>(ntl, 1));
+    double *d_part = V.take<double>((size_t)pl.G * 3 * natom);
+    if (opt.precision == TG_FP32) {
+        std::fill(route.begin(), route.end(), 1);
+    } else if (opt.precision == TG_MIXED_BOUND || opt.precision == TG_MIXED_LEARNED) {
+        std::vector<double> err(ntl);
+        if (opt.precision == TG_MIXED_BOUND) {
+            for (size_t i = 0; i < ntl; ++i) {
+                const int P = pl.qc_P[pl.tiles[i].qc], Qc = pl.qc_Q[pl.tiles[i].qc];
+                const int nfq = ncart(pc_la(P)) * ncart(pc_lb(P)) * ncart(pc_la(Qc)) * ncart(pc_lb(Qc));
+                err[i] = kEps32Bound * TILE * nfq * pl.tiles[i].bnd;
+            }
+        } else {
+            std::vector<size_t> all(ntl);
+            for (size_t i = 0; i < ntl; ++i) all[i] = i;
+            std::vector<float> pred;
+            rc = predict_tiles(b, pl, opt.router, all, st, d_ref, d_feat, d_pred, &pred, nullptr, launches);
+            if (rc != TG_OK) return rc;
+            for (size_t i = 0; i < ntl; ++i)
+                err[i] = (double)opt.router->eps_rel * TILE * std::pow(10.0, (double)pred[i] + opt.router->margin);
+        }
+        std::vector<size_t> ord(ntl);
+        for (size_t i = 0; i < ntl; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t u, size_t v) { return err[u] < err[v]; });
+        double acc = 0.0;
+        for (size_t i : ord) {
+            if (acc + err[i] > opt.mixed_tol) break;
+            acc += err[i];
+            route[i] = 1;
+        }
+    }
+    std::vector<std::vector<size_t>> lists(2 * NQC);
+    for (size_t i = 0; i < ntl; ++i) lists[2 * pl.tiles[i].qc + route[i]].push_back(i);
+    for (auto &L : lists)
+        std::stable_sort(L.begin(), L.end(),
+                         [&](size_t u, size_t v) { return pl.tiles[u].cost > pl.tiles[v].cost; });
+    TG_CUDA(cudaMemsetAsync(d_part, 0, sizeof(double) * (size_t)pl.G * 3 * natom, st));
+    TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 3 * NQC, st));
+    if (stats)
+        for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = 0.0;
+    rc = launch_lists(b, pl, lists, d_tiles, d_part, nullptr, opt.timing != 0, st, stats, launches);
+    if (rc != TG_OK) return rc;
+    k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, pl.G, d_part, pl.dgrad);
     ++launches;
     TG_CUDA(cudaGetLastError());
     unsigned long long hc[3 * NQC];
-    TG_CUDA(cudaMemcpyAsync(hc, dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    if (opt.device_ptrs) {
-        TG_CUDA(cudaMemcpyAsync(grad, dgrad, sizeof(double) * 3 * natom, cudaMemcpyDeviceToDevice, st));
-    } else {
-        TG_CUDA(cudaMemcpyAsync(grad, dgrad, sizeof(double) * 3 * natom, cudaMemcpyDeviceToHost, st));
-    }
+    TG_CUDA(cudaMemcpyAsync(hc, pl.dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaMemcpyAsync(grad, pl.dgrad, sizeof(double) * 3 * natom,
+                            opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     TG_CUDA(cudaStreamSynchronize(st));
     if (stats) {
         long long q = 0, pq = 0, q32 = 0;
         for (int qc = 0; qc < NQC; ++qc) {
             stats->class_quartets[qc] = (long long)hc[3 * qc];
             stats->class_prim_quartets[qc] = (long long)hc[3 * qc + 1];
-            if (!timed[qc]) stats->class_ms[qc] = 0.0;
             q += (long long)hc[3 * qc];
             pq += (long long)hc[3 * qc + 1];
             q32 += (long long)hc[3 * qc + 2];
@@ -616,12 +856,331 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
         stats->quartets = q;
         stats->prim_quartets = pq;
         stats->fp32_quartets = q32;
-        stats->pairs = npairs_kept;
-        stats->tiles = (long long)tiles_all.size();
+        stats->pairs = pl.npairs_kept;
+        stats->tiles = (long long)ntl;
         stats->launches = launches;
-        stats->grid = G;
+        stats->grid = pl.G;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    return TG_OK;
+}
+
+int tg_tile_samples(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_options *opt_in, int stride,
+                    int cap, float *features, float *target, float *err32, int *n_out)
+{
+    tg_basis *b = const_cast<tg_basis *>(cb);
+    if (!b || !pairs || !features || !target || !err32 || !n_out || stride < 1 || cap < 0) return TG_EINVAL;
+    tg_options opt;
+    if (opt_in) opt = *opt_in;
+    else tg_options_default(&opt);
+    cudaStream_t st = (cudaStream_t)opt.stream;
+    Plan pl;
+    int rc = make_plan(b, npair, pairs, opt, st, pl);
+    if (rc != TG_OK) return rc;
+    std::vector<size_t> pick;
+    for (size_t i = 0; i < pl.tiles.size() && (int)pick.size() < cap; i += stride) pick.push_back(i);
+    const size_t n = pick.size();
+    *n_out = (int)n;
+    if (!n) return TG_OK;
+    DevArena &V = b->ws2;
+    const size_t used2 = V.used;
+    // dump space: two precisions x n tiles x TILE x 12 doubles, plus the tile buffers
+    const size_t need = used2 + al(sizeof(uint2) * n) + al(sizeof(TileRef) * n) + al(sizeof(float) * n * (NFEAT + 1)) +
+                        2 * al(sizeof(double) * n * TILE * 12) + al(sizeof(double) * (size_t)pl.G * 3 * b->natom) + 8192;
+    if (need > V.cap) {
+        // grow the plan arena, then rebuild the plan inside it
+        TG_CUDA(cudaStreamSynchronize(st));
+        V.release();
+        TG_CUDA(V.reserve(need + need / 4));
+        return tg_tile_samples(cb, npair, pairs, opt_in, stride, cap, features, target, err32, n_out);
+    }
+    uint2 *d_tiles = V.take<uint2>(n);
+    TileRef *d_ref = V.take<TileRef>(n);
+    float *d_feat = V.take<float>(n * NFEAT);
+    float *d_pred = V.take<float>(n);
+    double *d64 = V.take<double>(n * TILE * 12);
+    double *d32 = V.take<double>(n * TILE * 12);
+    double *d_part = V.take<double>((size_t)pl.G * 3 * b->natom);
+    int launches = 0;
+    std::vector<float> feat;
+    rc = predict_tiles(b, pl, nullptr, pick, st, d_ref, d_feat, d_pred, nullptr, &feat, launches);
+    if (rc != TG_OK) return rc;
+    // samples in class order so every launch covers a contiguous dump range
+    std::vector<std::vector<size_t>> lists(2 * NQC);
+    std::vector<size_t> order;  // position of each sample in the dump
+    for (int r = 0; r < 2; ++r) {
+        for (auto &L : lists) L.clear();
+        for (size_t i : pick) lists[2 * pl.tiles[i].qc + r].push_back(i);
+        TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 3 * NQC, st));
+        TG_CUDA(cudaMemsetAsync(r ? d32 : d64, 0, sizeof(double) * n * TILE * 12, st));
+        rc = launch_lists(b, pl, lists, d_tiles, d_part, r ? d32 : d64, false, st, nullptr, launches);
+        if (rc != TG_OK) return rc;
+        TG_CUDA(cudaStreamSynchronize(st));
+    }
+    // dump position of sample k: class-major order of the lists
+    std::vector<size_t> pos(pl.tiles.size(), 0);
+    {
+        size_t p = 0;
+        for (int qc = 0; qc < NQC; ++qc)
+            for (size_t i : pick)
+                if (pl.tiles[i].qc == qc) pos[i] = p++;
+    }
+    std::vector<double> h64(n * TILE * 12), h32(n * TILE * 12);
+    TG_CUDA(cudaMemcpy(h64.data(), d64, sizeof(double) * h64.size(), cudaMemcpyDeviceToHost));
+    TG_CUDA(cudaMemcpy(h32.data(), d32, sizeof(double) * h32.size(), cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < n; ++k) {
+        const size_t p = pos[pick[k]];
+        double mx = 0.0, me = 0.0;
+        for (size_t j = p * TILE * 12; j < (p + 1) * TILE * 12; ++j) {
+            mx = std::max(mx, std::fabs(h64[j]));
+            me = std::max(me, std::fabs(h64[j] - h32[j]));
+        }
+        target[k] = (float)std::log10(mx + 1e-30);
+        err32[k] = (float)std::log10(me + 1e-30);
+        for (int f = 0; f < NFEAT; ++f) features[k * NFEAT + f] = feat[k * NFEAT + f];
+    }
+    return TG_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ router
+namespace {
+
+uint64_t splitmix64(uint64_t &x)
+{
+    uint64_t z = (x += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+struct DevBufs {
+    std::vector<void *> ptrs;
+    ~DevBufs()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    cudaError_t alloc(T **p, size_t n)
+    {
+        cudaError_t e = cudaMalloc((void **)p, sizeof(T) * std::max<size_t>(n, 1));
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int tg_router_nparam(void) { return NPARAM; }
+
+int tg_router_create(unsigned long long seed, tg_router **out)
+{
+    if (!out) return TG_EINVAL;
+    tg_router *r = new (std::nothrow) tg_router();
+    if (!r) return TG_ENOMEM;
+    uint64_t st = seed;
+    auto uni = [&]() { return (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); };
+    // Xavier-uniform weights, zero biases
+    int o = 0;
+    const int fan[3][2] = {{NFEAT, NH}, {NH, NH}, {NH, 1}};
+    for (int layer = 0; layer < 3; ++layer) {
+        const int fin = fan[layer][0], fout = fan[layer][1];
+        const double a = std::sqrt(6.0 / (fin + fout));
+        for (int k = 0; k < fin * fout; ++k) r->params[o++] = (float)((2.0 * uni() - 1.0) * a);
+        for (int k = 0; k < fout; ++k) r->params[o++] = 0.f;
+    }
+    for (int j = 0; j < NFEAT; ++j) {
+        r->mu[j] = 0.f;
+        r->sd[j] = 1.f;
+    }
+    *out = r;
+    return TG_OK;
+}
+
+void tg_router_destroy(tg_router *r) { delete r; }
+
+int tg_router_get(const tg_router *r, float *params, float *mu, float *sd, float *calib)
+{
+    if (!r) return TG_EINVAL;
+    if (params) std::memcpy(params, r->params, sizeof(r->params));
+    if (mu) std::memcpy(mu, r->mu, sizeof(r->mu));
+    if (sd) std::memcpy(sd, r->sd, sizeof(r->sd));
+    if (calib) {
+        calib[0] = r->margin;
+        calib[1] = r->eps_rel;
+        calib[2] = (float)r->trained;
+    }
+    return TG_OK;
+}
+
+int tg_router_set(tg_router *r, const float *params, const float *mu, const float *sd, const float *calib)
+{
+    if (!r) return TG_EINVAL;
+    if (params) std::memcpy(r->params, params, sizeof(r->params));
+    if (mu) std::memcpy(r->mu, mu, sizeof(r->mu));
+    if (sd) {
+        for (int j = 0; j < NFEAT; ++j)
+            if (!(sd[j] > 0.f)) return TG_EINVAL;
+        std::memcpy(r->sd, sd, sizeof(r->sd));
+    }
+    if (calib) {
+        if (!std::isfinite(calib[0]) || !(calib[1] >= 0.f)) return TG_EINVAL;
+        r->margin = calib[0];
+        r->eps_rel = calib[1];
+        r->trained = calib[2] != 0.f;
+    }
+    return TG_OK;
+}
+
+static int router_loss_grad_dev(const tg_router *r, int n, const float *dX, const float *dy, const float *dmu,
+                                const float *dsd, const float *dparams, float q, float *dgrad, float *dloss,
+                                float *gpart, float *lpart)
+{
+    const int nblk = (n + TRB - 1) / TRB;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bwd_smem());
+        attr = true;
+    }
+    k_mlp_fwd_bwd<<<nblk, TRB, fwd_bwd_smem()>>>(n, dX, dy, dmu, dsd, dparams, q, gpart, lpart);
+    k_sum_partials<<<(NPARAM + 127) / 128, 128>>>(nblk, NPARAM, gpart, dgrad);
+    k_sum_partials<<<1, 32>>>(nblk, 1, lpart, dloss);
+    TG_CUDA(cudaGetLastError());
+    (void)r;
+    return TG_OK;
+}
+
+// Training on the GPU: feature standardisation, then `epochs` full-batch
+// Adam steps on the expectile loss (quantile q) with a cosine learning-rate
+// decay.  loss_hist (nullable, epochs floats) receives the loss before each step.
+int tg_router_train(tg_router *r, int n, const float *X, const float *y, int epochs, float lr, float q,
+                    float *loss_hist)
+{
+    if (!r || n < 1 || !X || !y || epochs < 1 || !(lr > 0.f) || !(q > 0.f && q < 1.f)) return TG_EINVAL;
+    DevBufs B;
+    float *dX, *dy, *dmu, *dsd, *dp, *dm, *dv, *dg, *dl, *gpart, *lpart;
+    const int nblk = (n + TRB - 1) / TRB;
+    TG_CUDA(B.alloc(&dX, (size_t)n * NFEAT));
+    TG_CUDA(B.alloc(&dy, n));
+    TG_CUDA(B.alloc(&dmu, NFEAT));
+    TG_CUDA(B.alloc(&dsd, NFEAT));
+    TG_CUDA(B.alloc(&dp, NPARAM));
+    TG_CUDA(B.alloc(&dm, NPARAM));
+    TG_CUDA(B.alloc(&dv, NPARAM));
+    TG_CUDA(B.alloc(&dg, NPARAM));
+    TG_CUDA(B.alloc(&dl, epochs));
+    TG_CUDA(B.alloc(&gpart, (size_t)nblk * NPARAM));
+    TG_CUDA(B.alloc(&lpart, nblk));
+    TG_CUDA(cudaMemcpy(dX, X, sizeof(float) * n * NFEAT, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dy, y, sizeof(float) * n, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dp, r->params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemset(dm, 0, sizeof(float) * NPARAM));
+    TG_CUDA(cudaMemset(dv, 0, sizeof(float) * NPARAM));
+    k_feature_stats<<<1, 32>>>(n, dX, dmu, dsd);
+    TG_CUDA(cudaGetLastError());
+    for (int ep = 0; ep < epochs; ++ep) {
+        int rc = router_loss_grad_dev(r, n, dX, dy, dmu, dsd, dp, q, dg, dl + ep, gpart, lpart);
+        if (rc != TG_OK) return rc;
+        const float lr_t = lr * (0.05f + 0.95f * 0.5f * (1.f + std::cos(3.14159265f * ep / epochs)));
+        k_adam<<<(NPARAM + 127) / 128, 128>>>(NPARAM, dp, dg, dm, dv, lr_t, 0.9f, 0.999f, 1e-8f, ep + 1);
+    }
+    TG_CUDA(cudaGetLastError());
+    TG_CUDA(cudaMemcpy(r->params, dp, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    TG_CUDA(cudaMemcpy(r->mu, dmu, sizeof(float) * NFEAT, cudaMemcpyDeviceToHost));
+    TG_CUDA(cudaMemcpy(r->sd, dsd, sizeof(float) * NFEAT, cudaMemcpyDeviceToHost));
+    if (loss_hist) TG_CUDA(cudaMemcpy(loss_hist, dl, sizeof(float) * epochs, cudaMemcpyDeviceToHost));
+    return TG_OK;
+}
+
+// Loss and parameter gradient of the current router on (X, y) with the
+// router's own standardisation (for checks against an independent backprop).
+int tg_router_loss_grad(const tg_router *r, int n, const float *X, const float *y, float q, float *loss, float *grad)
+{
+    if (!r || n < 1 || !X || !y || !loss || !grad || !(q > 0.f && q < 1.f)) return TG_EINVAL;
+    DevBufs B;
+    float *dX, *dy, *dmu, *dsd, *dp, *dg, *dl, *gpart, *lpart;
+    const int nblk = (n + TRB - 1) / TRB;
+    TG_CUDA(B.alloc(&dX, (size_t)n * NFEAT));
+    TG_CUDA(B.alloc(&dy, n));
+    TG_CUDA(B.alloc(&dmu, NFEAT));
+    TG_CUDA(B.alloc(&dsd, NFEAT));
+    TG_CUDA(B.alloc(&dp, NPARAM));
+    TG_CUDA(B.alloc(&dg, NPARAM));
+    TG_CUDA(B.alloc(&dl, 1));
+    TG_CUDA(B.alloc(&gpart, (size_t)nblk * NPARAM));
+    TG_CUDA(B.alloc(&lpart, nblk));
+    TG_CUDA(cudaMemcpy(dX, X, sizeof(float) * n * NFEAT, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dy, y, sizeof(float) * n, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dmu, r->mu, sizeof(float) * NFEAT, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dsd, r->sd, sizeof(float) * NFEAT, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dp, r->params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+    int rc = router_loss_grad_dev(r, n, dX, dy, dmu, dsd, dp, q, dg, dl, gpart, lpart);
+    if (rc != TG_OK) return rc;
+    TG_CUDA(cudaMemcpy(grad, dg, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    TG_CUDA(cudaMemcpy(loss, dl, sizeof(float), cudaMemcpyDeviceToHost));
+    return TG_OK;
+}
+
+int tg_router_predict(const tg_router *r, int n, const float *X, float *out)
+{
+    if (!r || n < 1 || !X || !out) return TG_EINVAL;
+    DevBufs B;
+    float *dX, *dmu, *dsd, *dp, *dout;
+    TG_CUDA(B.alloc(&dX, (size_t)n * NFEAT));
+    TG_CUDA(B.alloc(&dmu, NFEAT));
+    TG_CUDA(B.alloc(&dsd, NFEAT));
+    TG_CUDA(B.alloc(&dp, NPARAM));
+    TG_CUDA(B.alloc(&dout, n));
+    TG_CUDA(cudaMemcpy(dX, X, sizeof(float) * n * NFEAT, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dmu, r->mu, sizeof(float) * NFEAT, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dsd, r->sd, sizeof(float) * NFEAT, cudaMemcpyHostToDevice));
+    TG_CUDA(cudaMemcpy(dp, r->params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+    k_mlp_predict<<<(n + 127) / 128, 128>>>(n, dX, dmu, dsd, dp, dout);
+    TG_CUDA(cudaGetLastError());
+    TG_CUDA(cudaMemcpy(out, dout, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return TG_OK;
+}
+
+// File: "TGRT", version 1, NFEAT, NH, then params, mu, sd, margin, eps_rel, trained.
+int tg_router_save(const tg_router *r, const char *path)
+{
+    if (!r || !path) return TG_EINVAL;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return TG_EINVAL;
+    const int hdr[4] = {0x54524754, 1, NFEAT, NH};
+    bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 && std::fwrite(r->params, sizeof(r->params), 1, f) == 1 &&
+              std::fwrite(r->mu, sizeof(r->mu), 1, f) == 1 && std::fwrite(r->sd, sizeof(r->sd), 1, f) == 1;
+    const float cal[3] = {r->margin, r->eps_rel, (float)r->trained};
+    ok = ok && std::fwrite(cal, sizeof(cal), 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? TG_OK : TG_EINVAL;
+}
+
+int tg_router_load(const char *path, tg_router **out)
+{
+    if (!path || !out) return TG_EINVAL;
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return TG_EROUTER;
+    int hdr[4];
+    tg_router *r = new (std::nothrow) tg_router();
+    float cal[3];
+    bool ok = r && std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 0x54524754 && hdr[1] == 1 &&
+              hdr[2] == NFEAT && hdr[3] == NH && std::fread(r->params, sizeof(r->params), 1, f) == 1 &&
+              std::fread(r->mu, sizeof(r->mu), 1, f) == 1 && std::fread(r->sd, sizeof(r->sd), 1, f) == 1 &&
+              std::fread(cal, sizeof(cal), 1, f) == 1;
+    std::fclose(f);
+    if (!ok) {
+        delete r;
+        return TG_EROUTER;
+    }
+    r->margin = cal[0];
+    r->eps_rel = cal[1];
+    r->trained = cal[2] != 0.f;
+    *out = r;
     return TG_OK;
 }
 

@@ -1,5 +1,5 @@
 // (pp|ps) derivative-ERI class kernel instance.
-#include "eri_grad.cuh"
+#include "eri_coop.cuh"
 
 namespace tg {
 

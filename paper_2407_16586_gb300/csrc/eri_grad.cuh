@@ -827,6 +827,12 @@ __global__ void __launch_bounds__(TILE) k_grad(GeoArgs geo, DensArgs den, Screen
                 npq += (unsigned long long)nbp * nkp;
             }
         }
+        if (out.dump) {
+            double *d = out.dump + ((size_t)it * TILE + threadIdx.x) * 12;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) d[k] = g[k];
+            continue;
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) stg[threadIdx.x * 12 + k] = g[k];
 #pragma unroll
@@ -861,7 +867,7 @@ __global__ void __launch_bounds__(TILE) k_grad(GeoArgs geo, DensArgs den, Screen
 }
 
 template <int LA, int LB, int LC, int LD>
-cudaError_t launch_class_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const GeoArgs &geo,
+cudaError_t launch_thread_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const GeoArgs &geo,
                                 const DensArgs &den, const ScreenArgs &scr, const ClassLaunch &cl, const OutArgs &out,
                                 const PrimPairs &pp, const double *boys)
 {

@@ -128,7 +128,7 @@ __device__ double self_repulsion(const double *h, int Lh, double rho)
 // (eq. deriv) on either centre, maximised over centre and direction.
 __global__ void k_schwarz(int npairs, const int2 *pairs, const double *xyz, const int *sh_atom, const int *sh_l,
                           const int *sh_nprim, const int *sh_poff, const double *exps, const double *cn, double *Q,
-                          double *Qd)
+                          double *Qd, const long long *bpoff, double *bp)
 {
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= npairs) return;
@@ -156,6 +156,7 @@ __global__ void k_schwarz(int npairs, const int2 *pairs, const double *xyz, cons
                 const double P = (za * A[d] + zb * B[d]) / p;
                 etab_rt(E[d], la + 1, lb + 1, P - A[d], P - B[d], 0.5 / p);
             }
+            double bmax = 0.0;
             for (int ia = 0; ia < na; ++ia)
                 for (int jb = 0; jb < nb; ++jb) {
                     int ax, ay, az, bx, by, bz;
@@ -192,8 +193,10 @@ __global__ void k_schwarz(int npairs, const int2 *pairs, const double *xyz, cons
                         s = sqrt(s > 0.0 ? s : 0.0) * cc;
                         if (var == 0) acc[ia * nb + jb] += s;
                         else accdv[ia * nb + jb][var - 1] += s;
+                        bmax = fmax(bmax, s);
                     }
                 }
+            bp[bpoff[ip] + ka * sh_nprim[b] + kb] = bmax;
         }
     double q = 0.0, qd = 0.0;
     for (int k = 0; k < na * nb; ++k) {
@@ -242,21 +245,54 @@ __global__ void k_rowmax(int nshell, const double *M, double *Mrow)
     Mrow[x] = m;
 }
 
-// Primitive-pair records of the kept shell pairs: p, P, K = c_a c_b
-// exp(-za zb/p |AB|^2), za (exponent on the pair's first shell).
-__global__ void k_prim_pairs(int npairs, const int *psa, const int *psb, const int *poff, const double *xyz,
-                             const int *sh_atom, const int *sh_nprim, const int *sh_poff, const double *exps,
-                             const double *cn, double *p_, double *Px, double *Py, double *Pz, double *K, double *za_,
-                             float *fp, float *fPx, float *fPy, float *fPz, float *fK, float *fza)
+// Primitive pairs of each kept shell pair that survive the primitive screen
+// (scale * b_kl * qq * Mmax^2 >= eps_p; every pair when eps_p <= 0).  b_kl
+// is stored per canonical pair (larger shell index first).
+__device__ __forceinline__ bool prim_keep(const double *bp, long long o, int ka, int kb, int Ka, int Kb, bool fwd,
+                                          double scale, double qq, double mmax, double eps_p)
+{
+    if (!(eps_p > 0.0)) return true;
+    const double b = bp[o + (fwd ? ka * Kb + kb : kb * Ka + ka)];
+    return !(scale * b * qq * mmax * mmax < eps_p);
+}
+
+__global__ void k_prim_count(int npairs, const int *psa, const int *psb, const int *key, const int *sh_nprim,
+                             const long long *bpoff, const double *bp, double scale, double qq, double mmax,
+                             double eps_p, int *np_out)
 {
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= npairs) return;
     const int a = psa[ip], b = psb[ip];
+    const int Ka = sh_nprim[a], Kb = sh_nprim[b];
+    const long long o = bpoff[key[ip]];
+    const bool fwd = a >= b;
+    int n = 0;
+    for (int ka = 0; ka < Ka; ++ka)
+        for (int kb = 0; kb < Kb; ++kb)
+            n += prim_keep(bp, o, ka, kb, Ka, Kb, fwd, scale, qq, mmax, eps_p) ? 1 : 0;
+    np_out[ip] = n;
+}
+
+// Primitive-pair records: p, P, K = c_a c_b exp(-za zb/p |AB|^2), za.
+__global__ void k_prim_pairs(int npairs, const int *psa, const int *psb, const int *poff, const int *key,
+                             const double *xyz, const int *sh_atom, const int *sh_nprim, const int *sh_poff,
+                             const double *exps, const double *cn, const long long *bpoff, const double *bp,
+                             double scale, double qq, double mmax, double eps_p, double *p_, double *Px, double *Py,
+                             double *Pz, double *K, double *za_, float *fp, float *fPx, float *fPy, float *fPz,
+                             float *fK, float *fza)
+{
+    const int ip = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= npairs) return;
+    const int a = psa[ip], b = psb[ip];
+    const int Ka = sh_nprim[a], Kb = sh_nprim[b];
+    const long long bo = bpoff[key[ip]];
+    const bool fwd = a >= b;
     const double *A = xyz + 3 * sh_atom[a], *B = xyz + 3 * sh_atom[b];
     const double AB2 = (A[0] - B[0]) * (A[0] - B[0]) + (A[1] - B[1]) * (A[1] - B[1]) + (A[2] - B[2]) * (A[2] - B[2]);
     int o = poff[ip];
-    for (int ka = 0; ka < sh_nprim[a]; ++ka)
-        for (int kb = 0; kb < sh_nprim[b]; ++kb) {
+    for (int ka = 0; ka < Ka; ++ka)
+        for (int kb = 0; kb < Kb; ++kb) {
+            if (!prim_keep(bp, bo, ka, kb, Ka, Kb, fwd, scale, qq, mmax, eps_p)) continue;
             const double za = exps[sh_poff[a] + ka], zb = exps[sh_poff[b] + kb];
             const double p = za + zb;
             const double k = cn[sh_poff[a] + ka] * cn[sh_poff[b] + kb] * exp(-za * zb / p * AB2);

@@ -86,6 +86,7 @@ struct OutArgs {
     double *partials;                 // [gridDim][natom*3], accumulated
     unsigned long long *counters;     // [0] quartets, [1] primitive quartets, [2] fp32 quartets
     int use_smem;                     // partial gradient kept in shared memory
+    double *dump;                     // nullable: per-quartet gradients [tile][TILE][12] instead of reducing
 };
 
 // ---------------------------------------------------------------- Boys

@@ -1,0 +1,53 @@
+"""Training pipeline of the learned block router.
+
+Samples quartet tiles of seeded training clusters (fp64 and fp32 evaluation
+of the same tiles, no reduction), trains the MLP on the GPU, and calibrates
+two constants on held-out tiles:
+
+* margin: the 99.9th percentile of (log10 true magnitude - prediction), so the
+  routed estimate 10^(prediction + margin) is rarely below the truth;
+* eps_rel: the 99.9th percentile of the fp32 error of a tile relative to its
+  largest fp64 contribution.
+
+TG_MIXED_LEARNED then sends a tile to fp32 only while the summed estimate
+eps_rel * 128 * 10^(prediction + margin) of all fp32 tiles stays within the
+call's mixed_tol (default 1e-6 Ha/bohr)."""
+from __future__ import annotations
+
+import numpy as np
+
+import paper_2407_16586_gb300 as tg
+
+
+def collect(systems, stride=40, cap=200000, screen_tol=1e-10):
+    Xs, ys, es = [], [], []
+    for s in systems:
+        b = tg.Basis(s)
+        X, y, e = b.tile_samples(s["pairs"], stride=stride, cap=cap, screen_tol=screen_tol)
+        b.close()
+        Xs.append(X)
+        ys.append(y)
+        es.append(e)
+    return np.concatenate(Xs), np.concatenate(ys), np.concatenate(es)
+
+
+def fit(X, y, e, seed=7, epochs=400, lr=1e-2, q=0.9, holdout=0.2, floor=-20.0):
+    """Train on (1 - holdout) of the tiles and calibrate on the rest.
+    Tiles whose contribution is below 10^floor carry no information about
+    routing and are clipped to the floor."""
+    y = np.maximum(y, floor).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    idx = rng.permutation(len(y))
+    nh = max(1, int(holdout * len(y)))
+    hold, tr = idx[:nh], idx[nh:]
+    r = tg.Router(seed=seed)
+    hist = r.train(X[tr], y[tr], epochs=epochs, lr=lr, q=q)
+    pred = r.predict(X[hold])
+    margin = float(max(0.0, np.quantile(y[hold] - pred, 0.999)))
+    rel = 10.0 ** (np.minimum(e, 0.0) - y)
+    keep = y > floor + 1
+    eps_rel = float(np.quantile(rel[keep], 0.999)) if keep.any() else 1e-5
+    r.set(calib=[margin, eps_rel, 1.0])
+    info = dict(n_train=len(tr), n_hold=nh, loss_first=float(hist[0]), loss_last=float(hist[-1]), margin=margin,
+                eps_rel=eps_rel, resid_hold_mean=float(np.mean(y[hold] - pred)))
+    return r, info

@@ -115,3 +115,16 @@ def test_error_codes(tg, c1):
     with pytest.raises(tg.TGError) as e:
         basis.grad2e([(a, a, 1, 0, 0, 0)], rank=2, nranks=2)
     assert e.value.status == tg.TG_EINVAL
+
+
+def test_fp32_route_close_to_fp64(tg, c1):
+    g64, _ = tg.grad2e(c1, screen_tol=1e-12)
+    g32, st = tg.grad2e(c1, screen_tol=1e-12, precision=tg.TG_FP32)
+    assert st["fp32_quartets"] == st["quartets"]
+    assert np.abs(g32 - g64).max() <= 1e-4
+
+
+def test_mixed_bound_meets_tolerance(tg, c1):
+    ref, _, _ = oracle.grad2e(c1, tau=1e-10)
+    g, st = tg.grad2e(c1, screen_tol=1e-10, precision=tg.TG_MIXED_BOUND)
+    assert np.abs(g - ref).max() <= 1e-6
