@@ -142,7 +142,7 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline(shards=400, shard=0):
+def cpu_baseline(shards=600, shard=0):
     import oracle
     from paper_2407_16586_gb300 import synth
     oracle.build()
@@ -155,14 +155,22 @@ def cpu_baseline(shards=400, shard=0):
             "sample": "shard %d of %d of the c2 quartets (%d quartets, %.1f s)" % (shard, shards, nq, dt)}
 
 
+def _flops_of(st, qc, fp32):
+    la, lb, lc, ld = class_ls()[qc]
+    npq = (st["class_prim_quartets_fp32"] if fp32 else st["class_prim_quartets"])[qc]
+    return npq, npq * flops_per_prim_quartet(la, lb, lc, ld)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
-    ap.add_argument("--ref-shards", type=int, default=400)
+    ap.add_argument("--precision", default="mixed-learned", choices=["mixed-learned", "mixed-bound", "fp64", "fp32"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed fp64 steps for the comparison (0: skip)")
+    ap.add_argument("--router", default=os.path.join(ROOT, "paper_2407_16586_gb300", "data", "router.bin"))
+    ap.add_argument("--ref-shards", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -187,6 +195,10 @@ def main():
     import paper_2407_16586_gb300 as tg
     from paper_2407_16586_gb300 import synth
 
+    prec = {"mixed-learned": tg.TG_MIXED_LEARNED, "mixed-bound": tg.TG_MIXED_BOUND, "fp64": tg.TG_FP64,
+            "fp32": tg.TG_FP32}[args.precision]
+    router = tg.Router(path=args.router) if prec == tg.TG_MIXED_LEARNED else None
+
     s = synth.config(1)
     basis = tg.Basis(s)
     dev = torch.device("cuda", local)
@@ -196,52 +208,53 @@ def main():
     gout = torch.empty((s["natom"], 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step(timing=False):
-        _, st = basis.grad2e(dpairs, screen_tol=TAU, out=gout, timing=timing)
+    def step(precision, timing=False):
+        _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=timing)
         return st
 
-    for _ in range(args.warmup):
-        st0 = step()
-    # per-class kernel times with CUDA events on the launching stream (timed separately)
-    st_t = step(timing=True)
+    def timed(precision, n):
+        total_ms, q, launches = 0.0, 0, 0
+        for _ in range(n):
+            flush.zero_()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step(precision)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            total_ms += e0.elapsed_time(e1)
+            q += st["quartets"]
+            launches += st["launches"]
+        return total_ms, q, launches, st
 
-    # ---- timed device-resident steps
+    for _ in range(args.warmup):
+        st0 = step(prec)
+    g_head = gout.cpu().numpy().copy()
+    # per-kernel times with CUDA events on the launching stream (separate call)
+    st_t = step(prec, timing=True)
+
     rows, stop = [], threading.Event()
     th = threading.Thread(target=_clock_sampler, args=(stop, rows), daemon=True)
     th.start()
     time.sleep(0.3)
-    total_ms = 0.0
-    quartets = 0
-    launches = 0
-    for _ in range(args.steps):
-        flush.zero_()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        total_ms += e0.elapsed_time(e1)
-        quartets += st["quartets"]
-        launches += st["launches"]
+    total_ms, quartets, launches, st_last = timed(prec, args.steps)
     stop.set()
     th.join(timeout=2)
     t_max = total_ms
+    quartets_all = float(quartets)
     if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        q = torch.tensor([quartets], device=dev, dtype=torch.float64)
-        dist.all_reduce(q)
-        quartets_all = float(q.item())
-    else:
-        quartets_all = float(quartets)
+        t = torch.tensor([total_ms, float(quartets)], device=dev, dtype=torch.float64)
+        tt = t.clone()
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t)
+        t_max = float(tt[0].item())
+        quartets_all = float(t[1].item())
     value = quartets_all / (t_max / 1e3)
 
-    # ---- end to end through the public API with host buffers
+    # end to end through the public API with host buffers (pinned)
     pin = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), cj, ck, cl, om)
            for (a, b, cj, ck, cl, om) in s["pairs"]]
     hpairs = [(a.numpy(), b.numpy(), cj, ck, cl, om) for (a, b, cj, ck, cl, om) in pin]
@@ -251,8 +264,8 @@ def main():
         flush.zero_()
         torch.cuda.synchronize(dev)
         t = time.perf_counter()
-        _, st = basis.grad2e(hpairs, screen_tol=TAU, out=hout, stream=stream.cuda_stream)
-        torch.cuda.synchronize(dev)
+        _, st = basis.grad2e(hpairs, screen_tol=TAU, precision=prec, router=router, out=hout,
+                             stream=stream.cuda_stream)
         e2e_ms += 1e3 * (time.perf_counter() - t)
         e2e_q += st["quartets"]
     if dist:
@@ -263,37 +276,59 @@ def main():
     h2d = sum(a.nbytes + b.nbytes for (a, b, *_r) in hpairs)
     d2h = hout.nbytes
 
+    # fp64 comparison (same workload, same clocks)
+    fp64 = None
+    if args.fp64_steps > 0 and prec != tg.TG_FP64:
+        step(tg.TG_FP64)
+        g64 = gout.cpu().numpy().copy()
+        ms64, q64, _, _ = timed(tg.TG_FP64, args.fp64_steps)
+        fp64 = {"ms_per_step": ms64 / args.fp64_steps, "value": q64 / (ms64 / 1e3),
+                "max_abs_dg_vs_fp64": float(np.abs(g_head - g64).max()),
+                "speedup_vs_fp64": (ms64 / args.fp64_steps) / (t_max / args.steps)}
+
     if rank == 0:
-        peaks = _peaks()
-        cls = class_ls()
-        per = [(st_t["class_ms"][qc], qc) for qc in range(21)]
-        ms, qc = max(per)
-        la, lb, lc, ld = cls[qc]
-        npq = st_t["class_prim_quartets"][qc]
-        flops = npq * flops_per_prim_quartet(la, lb, lc, ld)
-        achieved = flops / (ms / 1e3) / 1e12
-        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # 2 fp64 FMA / clk / SM at 2070 MHz
+        peaks = {"fp64": 152 * 2 * 2 * 2.07e9 / 1e12, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
         names = "spd"
-        kname = "k_grad_fp64<(%s%s|%s%s)>" % (names[la], names[lb], names[lc], names[ld])
+        best = None
+        for qc in range(21):
+            for fp32 in (False, True):
+                ms = (st_t["class_ms_fp32"] if fp32 else st_t["class_ms"])[qc]
+                if ms > 0 and (best is None or ms > best[0]):
+                    best = (ms, qc, fp32)
+        ms, qc, fp32 = best
+        npq, flops = _flops_of(st_t, qc, fp32)
+        la, lb, lc, ld = class_ls()[qc]
+        achieved = flops / (ms / 1e3) / 1e12
+        pk = peaks["fp32" if fp32 else "fp64"]
+        kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if (la, lb, lc, ld) in ((2, 2, 2, 2), (2, 2, 2, 1)) else "",
+                                               names[la], names[lb], names[lc], names[ld],
+                                               "fp32" if fp32 else "fp64")
+        tot_flops = sum(_flops_of(st_t, q, f)[1] for q in range(21) for f in (False, True))
+        tot_ms = sum(st_t["class_ms"]) + sum(st_t["class_ms_fp32"])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "screen_tol": TAU,
-                       "quartets_per_step": st0["quartets"], "prim_quartets_per_step": st0["prim_quartets"],
-                       "pairs": st0["pairs"], "tiles": st0["tiles"], "l2": "flushed (512 MB write) before each step",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "screen_tol": TAU, "mixed_tol": 1e-6,
+                       "quartets_per_step": st0["quartets"], "fp32_quartets_per_step": st0["fp32_quartets"],
+                       "prim_quartets_per_step": st0["prim_quartets"], "pairs": st0["pairs"], "tiles": st0["tiles"],
+                       "l2": "flushed (512 MB write) before each timed step",
                        "parallelism": "independent molecule per rank" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_q / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                         "peak_source": "fp64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF)",
-                         "class_ms": ms, "class_prim_quartets": npq},
+            "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                         "frac": achieved / pk, "traffic": None,
+                         "peak_source": "derived: 152 SM x (2 fp64 | 128 fp32) FMA/clk x 2 flop x 2.07 GHz",
+                         "kernel_ms": ms, "kernel_prim_quartets": npq,
+                         "all_kernels_tflops": tot_flops / (tot_ms / 1e3) / 1e12 if tot_ms > 0 else None},
             "clocks": _clocks_summary(rows, local),
         }
+        if fp64 is not None:
+            line["fp64"] = fp64
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(shards=args.ref_shards)
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -71,6 +71,7 @@ extern "C" {
 
 typedef struct tg_basis tg_basis;    /* opaque: basis + geometry, device copies */
 typedef struct tg_router tg_router;  /* opaque: block router MLP weights */
+typedef struct tg_batch tg_batch;    /* opaque: planned multi-molecule evaluation + CUDA graph */
 
 /* One density pair.  A and B are nbf*nbf doubles, row-major; host pointers
  * unless tg_options.device_ptrs is set, then device pointers. */
@@ -103,9 +104,11 @@ typedef struct {
     long long tiles;              /* quartet tiles launched */
     int launches;                 /* CUDA kernels launched by the call */
     int grid;                     /* CTAs of each persistent class launch */
-    double class_ms[21];          /* per angular class: kernel time (only with timing = 1) */
+    double class_ms[21];          /* per angular class: fp64 kernel time (only with timing = 1) */
+    double class_ms_fp32[21];     /* per angular class: fp32 kernel time (only with timing = 1) */
     long long class_quartets[21];
-    long long class_prim_quartets[21];
+    long long class_prim_quartets[21];       /* fp64 primitive quartets */
+    long long class_prim_quartets_fp32[21];  /* fp32 primitive quartets */
 } tg_stats;
 
 /* Fill o with the defaults listed above. */
@@ -130,20 +133,42 @@ int tg_grad2e(const tg_basis *b, int npair, const tg_pair *pairs, const tg_optio
 
 const char *tg_strerror(int status);
 
+/* ---- batched evaluation (many independent molecules, plan once, replay)
+ * tg_batch_create plans every molecule (screening, class sort, routing as in
+ * tg_grad2e) and captures one CUDA graph whose persistent class launches
+ * each cover the tiles of all molecules.  The bases must be distinct handles
+ * (a basis holds one plan at a time) and must outlive the batch; with
+ * device_ptrs the densities are read from the caller's device buffers at
+ * every run (their contents may change, the plan does not), otherwise they
+ * are copied at creation.  opt->reserved[0] = 1 autotunes the persistent
+ * grid (1-4 CTAs per SM) of every class list on a sample of its tiles.
+ * tg_batch_run replays the graph on opt->stream and writes grads[m]
+ * (natom_m * 3, host unless device_ptrs).  Not part of the paper, which
+ * evaluates one system at a time (Sec. II.C). */
+int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, const tg_pair *const *pairs,
+                    const tg_options *opt, tg_batch **out);
+int tg_batch_run(tg_batch *batch, double *const *grads, const tg_options *opt, tg_stats *stats);
+void tg_batch_destroy(tg_batch *batch);
+
 /* ---- learned block router (fp32 / fp64 routing only; it never skips work)
  * A 16-32-32-1 tanh perceptron maps 16 features of a quartet tile (angular
  * class, log10 of the tile's Schwarz x density bound, of Q and Q' on each
  * side, of the cross and pair density factors, pair-centre distances, pair
  * extents, smallest exponent sums, primitive-pair counts) to the log10 of the
- * tile's largest gradient contribution.  TG_MIXED_LEARNED routes a tile to
- * fp32 while the summed estimate eps_rel * 128 * 10^(prediction + margin)
- * stays within mixed_tol.  The paper has no counterpart: its kernels are
- * fp64 throughout (Sec. II.C, II.E). */
+ * tile's largest contribution to one gradient component.  Mixed modes route
+ * tiles to fp32 in increasing order of their error estimate e_t while
+ * sum e_t^2 <= (mixed_tol/3)^2 (independent rounding errors add in
+ * quadrature; 3 is the safety factor): e_t = eps_rel * 10^(prediction +
+ * margin) for TG_MIXED_LEARNED, 3e-6 * 128 * nfq * bound for TG_MIXED_BOUND.
+ * The paper has no counterpart: its kernels are fp64 throughout (Sec. II.C,
+ * II.E). */
 
 /* Per-tile training data: every stride-th screened tile (at most cap) of the
  * call's workload is evaluated in fp64 and in fp32 without reduction.
- * features: cap*16; target: log10 max |fp64 contribution| over the tile;
- * err32: log10 max |fp32 - fp64| over the tile; *n_out: tiles written. */
+ * features: cap*16; target: log10 of the tile's largest contribution to one
+ * gradient component (its quartets summed per atom and direction, fp64);
+ * err32: log10 of the largest |fp32 - fp64| difference of those sums;
+ * *n_out: tiles written. */
 int tg_tile_samples(const tg_basis *b, int npair, const tg_pair *pairs, const tg_options *opt, int stride, int cap,
                     float *features, float *target, float *err32, int *n_out);
 

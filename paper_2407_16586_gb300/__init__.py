@@ -35,7 +35,8 @@ TG_MAX_PAIRS = 8
 EXPORTS = ("tg_options_default", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
            "tg_grad2e", "tg_strerror", "tg_tile_samples", "tg_router_nparam", "tg_router_create",
            "tg_router_destroy", "tg_router_get", "tg_router_set", "tg_router_train", "tg_router_loss_grad",
-           "tg_router_predict", "tg_router_save", "tg_router_load")
+           "tg_router_predict", "tg_router_save", "tg_router_load", "tg_batch_create", "tg_batch_run",
+           "tg_batch_destroy")
 NFEAT = 16
 
 
@@ -55,7 +56,9 @@ class tg_stats(ctypes.Structure):
     _fields_ = [("seconds", ctypes.c_double), ("quartets", ctypes.c_longlong), ("prim_quartets", ctypes.c_longlong),
                 ("fp32_quartets", ctypes.c_longlong), ("pairs", ctypes.c_longlong), ("tiles", ctypes.c_longlong),
                 ("launches", ctypes.c_int), ("grid", ctypes.c_int), ("class_ms", ctypes.c_double * 21),
-                ("class_quartets", ctypes.c_longlong * 21), ("class_prim_quartets", ctypes.c_longlong * 21)]
+                ("class_ms_fp32", ctypes.c_double * 21), ("class_quartets", ctypes.c_longlong * 21),
+                ("class_prim_quartets", ctypes.c_longlong * 21),
+                ("class_prim_quartets_fp32", ctypes.c_longlong * 21)]
 
     def as_dict(self):
         out = {}
@@ -112,7 +115,12 @@ def lib():
         L.tg_router_predict.argtypes = [vp, ctypes.c_int, fp, fp]
         L.tg_router_save.argtypes = [vp, ctypes.c_char_p]
         L.tg_router_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
-        for n in ("tg_tile_samples", "tg_router_nparam", "tg_router_create", "tg_router_get", "tg_router_set",
+        L.tg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ip, ctypes.POINTER(ctypes.POINTER(tg_pair)),
+                                      ctypes.POINTER(tg_options), ctypes.POINTER(vp)]
+        L.tg_batch_run.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(tg_options), ctypes.POINTER(tg_stats)]
+        L.tg_batch_destroy.argtypes = [vp]
+        L.tg_batch_destroy.restype = None
+        for n in ("tg_batch_create", "tg_batch_run", "tg_tile_samples", "tg_router_nparam", "tg_router_create", "tg_router_get", "tg_router_set",
                   "tg_router_train", "tg_router_loss_grad", "tg_router_predict", "tg_router_save",
                   "tg_router_load"):
             getattr(L, n).restype = ctypes.c_int
@@ -348,3 +356,62 @@ class Router:
         rc = lib().tg_router_save(self.h, os.fsencode(path))
         if rc != TG_OK:
             raise TGError(rc, "tg_router_save")
+
+
+class Batch:
+    """Planned evaluation of many independent molecules (tg_batch_*): every
+    molecule keeps its own Basis; run() replays one captured CUDA graph."""
+
+    def __init__(self, systems, screen_tol=1e-10, precision=TG_FP64, router=None, mixed_tol=1e-6, autotune=False,
+                 device=None):
+        self.bases = [Basis(s) for s in systems]
+        self.natoms = [int(s["natom"]) for s in systems]
+        self._keep = []
+        opt = tg_options_default()
+        opt.screen_tol = float(screen_tol)
+        opt.precision = int(precision)
+        opt.mixed_tol = float(mixed_tol)
+        if router is not None:
+            opt.router = router.h
+        if autotune:
+            opt.reserved[0] = 1
+        parrs = []
+        for s, b in zip(systems, self.bases):
+            keep, plist = b._plist(s["pairs"])
+            self._keep.append(keep)
+            parrs.append((tg_pair * len(plist))(*[tg_pair(*p) for p in plist]))
+        self._parrs = parrs
+        n = len(systems)
+        hs = (ctypes.c_void_p * n)(*[b.h for b in self.bases])
+        npair = np.array([len(s["pairs"]) for s in systems], dtype=np.int32)
+        pp = (ctypes.POINTER(tg_pair) * n)(*[ctypes.cast(a, ctypes.POINTER(tg_pair)) for a in parrs])
+        self.h = ctypes.c_void_p()
+        rc = lib().tg_batch_create(n, hs, npair.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), pp, ctypes.byref(opt),
+                                   ctypes.byref(self.h))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_batch_create")
+
+    def run(self, stream=None):
+        outs = [np.zeros((n, 3)) for n in self.natoms]
+        ptrs = (ctypes.c_void_p * len(outs))(*[o.ctypes.data for o in outs])
+        opt = tg_options_default()
+        if stream is not None:
+            opt.stream = ctypes.c_void_p(stream)
+        st = tg_stats()
+        rc = lib().tg_batch_run(self.h, ptrs, ctypes.byref(opt), ctypes.byref(st))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_batch_run")
+        return outs, st.as_dict()
+
+    def close(self):
+        if self.h is not None:
+            lib().tg_batch_destroy(self.h)
+            self.h = None
+        for b in self.bases:
+            b.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

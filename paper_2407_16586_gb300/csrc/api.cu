@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -121,7 +122,7 @@ int basis_setup(tg_basis *b, const double *xyz, const double *exps, const double
     TG_CUDA(cudaMalloc(&b->d_exps, sizeof(double) * np));
     TG_CUDA(cudaMalloc(&b->d_coefs, sizeof(double) * np));
     TG_CUDA(cudaMalloc(&b->d_cn, sizeof(double) * np));
-    TG_CUDA(cudaMalloc(&b->d_boys, sizeof(double) * BOYS_NG * (BOYS_M + 1)));
+    TG_CUDA(cudaMalloc(&b->d_boys, (sizeof(double) + sizeof(float)) * BOYS_TAB));
     TG_CUDA(cudaMalloc(&b->d_router, sizeof(float) * (NPARAM + 2 * NFEAT)));
     TG_CUDA(cudaMalloc(&b->d_sh_atom, sizeof(int) * ns));
     TG_CUDA(cudaMalloc(&b->d_sh_l, sizeof(int) * ns));
@@ -389,7 +390,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
     const int nmat_up = opt.device_ptrs ? 0 : 2 * npair;
     const size_t need1 = al(sizeof(double) * nbf2) * (nmat_up + 2 * npair) + al(sizeof(double) * (size_t)ns * ns) +
                          al(sizeof(double) * ns) + al(sizeof(double) * TG_MAX_PAIRS) +
-                         al(sizeof(double) * 3 * natom) + al(sizeof(unsigned long long) * 3 * NQC) + 4096;
+                         al(sizeof(double) * 3 * natom) + al(sizeof(unsigned long long) * 4 * NQC) + 4096;
     TG_CUDA(W.reserve(need1));
     W.used = 0;
     double *dmat[2 * TG_MAX_PAIRS], *dS[2 * TG_MAX_PAIRS];
@@ -399,7 +400,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
     pl.dMrow = W.take<double>(ns);
     double *dw = W.take<double>(TG_MAX_PAIRS);
     pl.dgrad = W.take<double>(3 * natom);
-    pl.dcnt = W.take<unsigned long long>(3 * NQC);
+    pl.dcnt = W.take<unsigned long long>(4 * NQC);
     for (int p = 0; p < npair; ++p) {
         if (opt.device_ptrs) {
             den.A[p] = pairs[p].A;
@@ -476,7 +477,8 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
                 ntl_max += (long long)((pl.cls[P].size() + TB - 1) / TB) * ((pl.cls[Qc].size() + TK - 1) / TK);
         const size_t ntl = (size_t)std::max<long long>(ntl_max, 1);
         const size_t need2 = 6 * al(sizeof(int) * np_k) + 2 * al(sizeof(double) * np_k) +
-                             6 * al(sizeof(double) * npp) + 6 * al(sizeof(float) * npp) + al(sizeof(uint2) * ntl) +
+                             6 * al(sizeof(double) * npp) + 12 * al(sizeof(float) * npp) + al(sizeof(uint4) * ntl) +
+                             al(sizeof(MolDesc)) +
                              al(sizeof(TileRef) * ntl) + al(sizeof(float) * ntl * (NFEAT + 1)) +
                              al(sizeof(double) * (size_t)pl.G * 3 * natom) + 8192;
         DevArena &V = b->ws2;
@@ -594,6 +596,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
            *pp_z = V.take<double>(npp), *pp_K = V.take<double>(npp), *pp_za = V.take<double>(npp);
     float *fp_p = V.take<float>(npp), *fp_x = V.take<float>(npp), *fp_y = V.take<float>(npp),
           *fp_z = V.take<float>(npp), *fp_K = V.take<float>(npp), *fp_za = V.take<float>(npp);
+    float *fp_PA = V.take<float>(3 * npp), *fp_PB = V.take<float>(3 * npp);
     const long long nk = pl.npairs_kept;
     if (nk > 0) {
         TG_CUDA(cudaMemcpyAsync(pl.d_sa, h_sa.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
@@ -606,7 +609,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
         k_prim_pairs<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(
             (int)nk, pl.d_sa, pl.d_sb, pl.d_poff, pl.d_key, b->d_xyz, b->d_sh_atom, b->d_sh_nprim, b->d_sh_poff,
             b->d_exps, b->d_cn, b->d_bpoff, b->d_bp, scale, qq, Mmax, eps_p, pp_p, pp_x, pp_y, pp_z, pp_K, pp_za, fp_p,
-            fp_x, fp_y, fp_z, fp_K, fp_za);
+            fp_x, fp_y, fp_z, fp_K, fp_za, fp_PA, fp_PB, (long long)npp);
         ++pl.launches;
         TG_CUDA(cudaGetLastError());
         // the host pair vectors must outlive the asynchronous copies
@@ -624,6 +627,9 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
     pl.pp.fPz = fp_z;
     pl.pp.fK = fp_K;
     pl.pp.fza = fp_za;
+    pl.pp.fPA = fp_PA;
+    pl.pp.fPB = fp_PB;
+    pl.pp.n = (long long)npp;
     pl.geo.natom = natom;
     pl.geo.nshell = ns;
     pl.geo.xyz = b->d_xyz;
@@ -692,27 +698,114 @@ int predict_tiles(tg_basis *b, const Plan &pl, const tg_router *r, const std::ve
     return TG_OK;
 }
 
-// Launch the class kernels over per-(class, precision) tile lists.  With
-// dump != nullptr every quartet's 12 gradient components are written to
-// dump[(list position * TILE + thread) * 12 + k] instead of being reduced.
-int launch_lists(tg_basis *b, Plan &pl, const std::vector<std::vector<size_t>> &lists, uint2 *d_tiles,
-                 double *d_part, double *dump, bool timing, cudaStream_t st, tg_stats *stats, int &launches)
+// Routing of one molecule's tiles.  e_t estimates tile t's fp32 error in any
+// single gradient component: eps * (every gradient component of a quartet is
+// at most nfq * bound, and a tile holds TILE quartets) for the bound router,
+// eps_rel * 10^(prediction + margin) for the learned router, whose prediction
+// is the tile's largest contribution to one gradient component.  Tiles go to
+// fp32 in increasing e_t while sum e_t^2 stays within (mixed_tol / 3)^2: the
+// fp32 rounding errors of different tiles are independent, so they add in
+// quadrature, and the factor 3 is the safety margin of that model.
+int compute_route(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_t st, TileRef *d_ref, float *d_feat,
+                  float *d_pred, std::vector<uint8_t> &route, int &launches)
 {
-    std::vector<uint2> flat;
-    std::vector<long long> off(2 * NQC + 1);
-    for (int k = 0; k < 2 * NQC; ++k) {
-        off[k] = (long long)flat.size();
-        for (size_t i : lists[k]) flat.push_back(make_uint2(pl.tiles[i].bt, pl.tiles[i].kt));
+    const size_t ntl = pl.tiles.size();
+    route.assign(ntl, 0);
+    if (opt.precision == TG_FP32) {
+        std::fill(route.begin(), route.end(), 1);
+    } else if (opt.precision == TG_MIXED_BOUND || opt.precision == TG_MIXED_LEARNED) {
+        std::vector<double> err(ntl);
+        if (opt.precision == TG_MIXED_BOUND) {
+            for (size_t i = 0; i < ntl; ++i) {
+                const int P = pl.qc_P[pl.tiles[i].qc], Qc = pl.qc_Q[pl.tiles[i].qc];
+                const int nfq = ncart(pc_la(P)) * ncart(pc_lb(P)) * ncart(pc_la(Qc)) * ncart(pc_lb(Qc));
+                err[i] = kEps32Bound * TILE * nfq * pl.tiles[i].bnd;
+            }
+        } else {
+            std::vector<size_t> all(ntl);
+            for (size_t i = 0; i < ntl; ++i) all[i] = i;
+            std::vector<float> pred;
+            int rc = predict_tiles(b, pl, opt.router, all, st, d_ref, d_feat, d_pred, &pred, nullptr, launches);
+            if (rc != TG_OK) return rc;
+            for (size_t i = 0; i < ntl; ++i)
+                err[i] = (double)opt.router->eps_rel * std::pow(10.0, (double)pred[i] + opt.router->margin);
+        }
+        std::vector<size_t> ord(ntl);
+        for (size_t i = 0; i < ntl; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t u, size_t v) { return err[u] < err[v]; });
+        const double budget = (opt.mixed_tol / 3.0) * (opt.mixed_tol / 3.0);
+        double acc = 0.0;
+        for (size_t i : ord) {
+            if (acc + err[i] * err[i] > budget) break;
+            acc += err[i] * err[i];
+            route[i] = 1;
+        }
     }
-    off[2 * NQC] = (long long)flat.size();
-    if (!flat.empty())
-        TG_CUDA(cudaMemcpyAsync(d_tiles, flat.data(), sizeof(uint2) * flat.size(), cudaMemcpyHostToDevice, st));
-    const int natom = b->natom;
+    return TG_OK;
+}
+
+MolDesc make_desc(const Plan &pl, int atom_off)
+{
+    MolDesc md;
+    std::memset(&md, 0, sizeof(md));
+    md.geo = pl.geo;
+    md.den = pl.den;
+    md.scr = pl.scr;
+    md.pp = pl.pp;
+    for (int c = 0; c < NPC; ++c) md.sets[c] = pl.set(c);
+    md.atom_off = atom_off;
+    return md;
+}
+
+// Tiles of a batch per (class, precision), grouped by molecule, each
+// molecule's tiles sorted by decreasing cost.
+struct Exec {
+    std::vector<uint4> tiles;
+    long long off[2 * NQC + 1];
+    int natom_total = 0, natom_max = 0;
+};
+
+void build_exec(const std::vector<const Plan *> &plans, const std::vector<std::vector<uint8_t>> &routes,
+                const std::vector<std::vector<size_t>> *subset, Exec &ex)
+{
+    ex.tiles.clear();
+    std::vector<std::vector<std::vector<size_t>>> lists(plans.size(), std::vector<std::vector<size_t>>(2 * NQC));
+    for (size_t m = 0; m < plans.size(); ++m) {
+        const Plan &pl = *plans[m];
+        if (subset) {
+            for (size_t i : (*subset)[m]) lists[m][2 * pl.tiles[i].qc + routes[m][i]].push_back(i);
+        } else {
+            for (size_t i = 0; i < pl.tiles.size(); ++i) lists[m][2 * pl.tiles[i].qc + routes[m][i]].push_back(i);
+        }
+        if (!subset)
+            for (auto &L : lists[m])
+                std::stable_sort(L.begin(), L.end(),
+                                 [&](size_t u, size_t v) { return pl.tiles[u].cost > pl.tiles[v].cost; });
+    }
+    for (int k = 0; k < 2 * NQC; ++k) {
+        ex.off[k] = (long long)ex.tiles.size();
+        for (size_t m = 0; m < plans.size(); ++m)
+            for (size_t i : lists[m][k])
+                ex.tiles.push_back(make_uint4((unsigned)m, plans[m]->tiles[i].bt, plans[m]->tiles[i].kt, 0u));
+    }
+    ex.off[2 * NQC] = (long long)ex.tiles.size();
+}
+
+// Class launches over an uploaded Exec.  grids[k] (nullable) overrides the
+// persistent grid of list k; with dump != nullptr every quartet's 12
+// components go to dump[(list position * TILE + thread) * 12 + c].
+int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, double *d_part,
+                unsigned long long *dcnt, double *dump, const double *boys, int G, const int *grids, bool timing,
+                cudaStream_t st, tg_stats *stats, int &launches)
+{
     OutArgs out;
     out.partials = d_part;
+    out.natom_total = ex.natom_total;
+    out.natom_max = ex.natom_max;
     out.dump = dump;
-    const size_t stage = (size_t)TILE * 12 * sizeof(double) + (size_t)TILE * 4 * sizeof(int);
-    const size_t sgrad = (size_t)3 * natom * sizeof(double);
+    const size_t stage = (size_t)TILE * 12 * sizeof(double) + (size_t)TILE * 4 * sizeof(int) +
+                         6 * (TB + TK) * sizeof(double) + 2 * (TB + TK) * sizeof(int);
+    const size_t sgrad = (size_t)3 * ex.natom_max * sizeof(double);
     out.use_smem = (stage + sgrad) <= 160 * 1024;
     const size_t smem = stage + (out.use_smem ? sgrad : 0);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -722,38 +815,42 @@ int launch_lists(tg_basis *b, Plan &pl, const std::vector<std::vector<size_t>> &
     }
     int rc = TG_OK;
     for (int qc = 0; qc < NQC && rc == TG_OK; ++qc) {
-        bool any = false;
         for (int r = 0; r < 2; ++r) {
-            const long long nt = off[2 * qc + r + 1] - off[2 * qc + r];
+            const int k = 2 * qc + r;
+            const long long nt = ex.off[k + 1] - ex.off[k];
             if (nt <= 0) continue;
             ClassLaunch cl;
-            cl.bra = pl.set(pl.qc_P[qc]);
-            cl.ket = pl.set(pl.qc_Q[qc]);
-            cl.same = pl.qc_P[qc] == pl.qc_Q[qc];
+            int Pc = 0, Qc = 0;
+            for (int a = 0; a < NPC; ++a)
+                for (int c = 0; c <= a; ++c)
+                    if (a * (a + 1) / 2 + c == qc) {
+                        Pc = a;
+                        Qc = c;
+                    }
+            cl.P = Pc;
+            cl.Q = Qc;
             cl.ntiles = nt;
-            cl.tiles = d_tiles + off[2 * qc + r];
-            cl.route = nullptr;
+            cl.tiles = d_tiles + ex.off[k];
             OutArgs o = out;
-            o.counters = pl.dcnt + 3 * qc;
-            if (dump) o.dump = dump + (size_t)off[2 * qc + r] * TILE * 12;
-            const int grid = (int)std::min<long long>(nt, pl.G);
-            if (timing && !any) cudaEventRecord(e0, st);
-            cudaError_t e =
-                kClassLaunchers[qc](r, grid, smem, st, pl.geo, pl.den, pl.scr, cl, o, pl.pp, b->d_boys);
+            o.counters = dcnt + 4 * qc;
+            if (dump) o.dump = dump + (size_t)ex.off[k] * TILE * 12;
+            const int g0 = (grids && grids[k] > 0) ? grids[k] : G;
+            const int grid = (int)std::min<long long>(nt, g0);
+            if (timing) cudaEventRecord(e0, st);
+            cudaError_t e = kClassLaunchers[qc](r, grid, smem, st, d_mols, cl, o, boys);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 rc = TG_ECUDA;
                 break;
             }
-            any = true;
             ++launches;
-        }
-        if (timing && any && rc == TG_OK) {
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (stats) stats->class_ms[qc] = ms;
+            if (timing) {
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (stats) (r ? stats->class_ms_fp32 : stats->class_ms)[qc] += ms;
+            }
         }
     }
     if (timing) {
@@ -763,7 +860,52 @@ int launch_lists(tg_basis *b, Plan &pl, const std::vector<std::vector<size_t>> &
     return rc;
 }
 
+void fill_stats(tg_stats *stats, const unsigned long long *hc, long long pairs, long long tiles, int launches, int G)
+{
+    if (!stats) return;
+    long long q = 0, pq = 0, q32 = 0;
+    for (int qc = 0; qc < NQC; ++qc) {
+        stats->class_quartets[qc] = (long long)hc[4 * qc];
+        stats->class_prim_quartets[qc] = (long long)hc[4 * qc + 1];
+        stats->class_prim_quartets_fp32[qc] = (long long)hc[4 * qc + 3];
+        q += (long long)hc[4 * qc];
+        pq += (long long)hc[4 * qc + 1] + (long long)hc[4 * qc + 3];
+        q32 += (long long)hc[4 * qc + 2];
+    }
+    stats->quartets = q;
+    stats->prim_quartets = pq;
+    stats->fp32_quartets = q32;
+    stats->pairs = pairs;
+    stats->tiles = tiles;
+    stats->launches = launches;
+    stats->grid = G;
+}
+
 }  // namespace
+
+struct tg_batch;
+extern "C" void tg_batch_destroy(tg_batch *bt);
+
+struct tg_batch {
+    int nmol = 0;
+    std::vector<tg_basis *> bases;
+    std::vector<Plan> plans;
+    Exec ex;
+    DevArena arena;
+    MolDesc *d_mols = nullptr;
+    uint4 *d_tiles = nullptr;
+    double *d_part = nullptr, *d_grad = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    std::vector<int> grids;
+    int G = 1;
+    int device_ptrs = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long pairs = 0;
+    int launches = 0;
+    std::vector<int> atom_off;
+};
 
 extern "C" {
 
@@ -783,83 +925,41 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
     if (rc != TG_OK) return rc;
     const int natom = b->natom;
     int launches = pl.launches;
-
-    // ---- routing: fp32 for the tiles with the smallest error estimate while
-    // the summed estimate stays within mixed_tol.  Estimates: every gradient
-    // component of a quartet is at most nfq * bound (bound router) or
-    // 10^(prediction + margin) (learned router); fp32 errs by eps_rel of that.
     const size_t ntl = pl.tiles.size();
-    std::vector<uint8_t> route(ntl, 0);
     DevArena &V = b->ws2;
-    uint2 *d_tiles = V.take<uint2>(std::max<size_t>(ntl, 1));
+    uint4 *d_tiles = V.take<uint4>(std::max<size_t>(ntl, 1));
     TileRef *d_ref = V.take<TileRef>(std::max<size_t>(ntl, 1));
     float *d_feat = V.take<float>(std::max<size_t>(ntl, 1) * NFEAT);
     float *d_pred = V.take<float>(std::max<size_t>(ntl, 1));
     double *d_part = V.take<double>((size_t)pl.G * 3 * natom);
-    if (opt.precision == TG_FP32) {
-        std::fill(route.begin(), route.end(), 1);
-    } else if (opt.precision == TG_MIXED_BOUND || opt.precision == TG_MIXED_LEARNED) {
-        std::vector<double> err(ntl);
-        if (opt.precision == TG_MIXED_BOUND) {
-            for (size_t i = 0; i < ntl; ++i) {
-                const int P = pl.qc_P[pl.tiles[i].qc], Qc = pl.qc_Q[pl.tiles[i].qc];
-                const int nfq = ncart(pc_la(P)) * ncart(pc_lb(P)) * ncart(pc_la(Qc)) * ncart(pc_lb(Qc));
-                err[i] = kEps32Bound * TILE * nfq * pl.tiles[i].bnd;
-            }
-        } else {
-            std::vector<size_t> all(ntl);
-            for (size_t i = 0; i < ntl; ++i) all[i] = i;
-            std::vector<float> pred;
-            rc = predict_tiles(b, pl, opt.router, all, st, d_ref, d_feat, d_pred, &pred, nullptr, launches);
-            if (rc != TG_OK) return rc;
-            for (size_t i = 0; i < ntl; ++i)
-                err[i] = (double)opt.router->eps_rel * TILE * std::pow(10.0, (double)pred[i] + opt.router->margin);
-        }
-        std::vector<size_t> ord(ntl);
-        for (size_t i = 0; i < ntl; ++i) ord[i] = i;
-        std::stable_sort(ord.begin(), ord.end(), [&](size_t u, size_t v) { return err[u] < err[v]; });
-        double acc = 0.0;
-        for (size_t i : ord) {
-            if (acc + err[i] > opt.mixed_tol) break;
-            acc += err[i];
-            route[i] = 1;
-        }
-    }
-    std::vector<std::vector<size_t>> lists(2 * NQC);
-    for (size_t i = 0; i < ntl; ++i) lists[2 * pl.tiles[i].qc + route[i]].push_back(i);
-    for (auto &L : lists)
-        std::stable_sort(L.begin(), L.end(),
-                         [&](size_t u, size_t v) { return pl.tiles[u].cost > pl.tiles[v].cost; });
+    MolDesc *d_mol = V.take<MolDesc>(1);
+    std::vector<std::vector<uint8_t>> routes(1);
+    rc = compute_route(b, pl, opt, st, d_ref, d_feat, d_pred, routes[0], launches);
+    if (rc != TG_OK) return rc;
+    Exec ex;
+    build_exec({&pl}, routes, nullptr, ex);
+    ex.natom_total = ex.natom_max = natom;
+    const MolDesc md = make_desc(pl, 0);
+    TG_CUDA(cudaMemcpyAsync(d_mol, &md, sizeof(MolDesc), cudaMemcpyHostToDevice, st));
+    if (!ex.tiles.empty())
+        TG_CUDA(cudaMemcpyAsync(d_tiles, ex.tiles.data(), sizeof(uint4) * ex.tiles.size(), cudaMemcpyHostToDevice, st));
     TG_CUDA(cudaMemsetAsync(d_part, 0, sizeof(double) * (size_t)pl.G * 3 * natom, st));
-    TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 3 * NQC, st));
+    TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 4 * NQC, st));
     if (stats)
-        for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = 0.0;
-    rc = launch_lists(b, pl, lists, d_tiles, d_part, nullptr, opt.timing != 0, st, stats, launches);
+        for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
+    rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, nullptr, b->d_boys, pl.G, nullptr, opt.timing != 0, st,
+                     stats, launches);
     if (rc != TG_OK) return rc;
     k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, pl.G, d_part, pl.dgrad);
     ++launches;
     TG_CUDA(cudaGetLastError());
-    unsigned long long hc[3 * NQC];
+    unsigned long long hc[4 * NQC];
     TG_CUDA(cudaMemcpyAsync(hc, pl.dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
     TG_CUDA(cudaMemcpyAsync(grad, pl.dgrad, sizeof(double) * 3 * natom,
                             opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     TG_CUDA(cudaStreamSynchronize(st));
     if (stats) {
-        long long q = 0, pq = 0, q32 = 0;
-        for (int qc = 0; qc < NQC; ++qc) {
-            stats->class_quartets[qc] = (long long)hc[3 * qc];
-            stats->class_prim_quartets[qc] = (long long)hc[3 * qc + 1];
-            q += (long long)hc[3 * qc];
-            pq += (long long)hc[3 * qc + 1];
-            q32 += (long long)hc[3 * qc + 2];
-        }
-        stats->quartets = q;
-        stats->prim_quartets = pq;
-        stats->fp32_quartets = q32;
-        stats->pairs = pl.npairs_kept;
-        stats->tiles = (long long)ntl;
-        stats->launches = launches;
-        stats->grid = pl.G;
+        fill_stats(stats, hc, pl.npairs_kept, (long long)ntl, launches, pl.G);
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return TG_OK;
@@ -883,10 +983,9 @@ int tg_tile_samples(const tg_basis *cb, int npair, const tg_pair *pairs, const t
     *n_out = (int)n;
     if (!n) return TG_OK;
     DevArena &V = b->ws2;
-    const size_t used2 = V.used;
-    // dump space: two precisions x n tiles x TILE x 12 doubles, plus the tile buffers
-    const size_t need = used2 + al(sizeof(uint2) * n) + al(sizeof(TileRef) * n) + al(sizeof(float) * n * (NFEAT + 1)) +
-                        2 * al(sizeof(double) * n * TILE * 12) + al(sizeof(double) * (size_t)pl.G * 3 * b->natom) + 8192;
+    const size_t need = V.used + al(sizeof(uint4) * n) + al(sizeof(TileRef) * n) + al(sizeof(float) * n * (NFEAT + 1)) +
+                        2 * al(sizeof(double) * n * TILE * 12) + al(sizeof(double) * (size_t)pl.G * 3 * b->natom) +
+                        al(sizeof(MolDesc)) + 8192;
     if (need > V.cap) {
         // grow the plan arena, then rebuild the plan inside it
         TG_CUDA(cudaStreamSynchronize(st));
@@ -894,30 +993,36 @@ int tg_tile_samples(const tg_basis *cb, int npair, const tg_pair *pairs, const t
         TG_CUDA(V.reserve(need + need / 4));
         return tg_tile_samples(cb, npair, pairs, opt_in, stride, cap, features, target, err32, n_out);
     }
-    uint2 *d_tiles = V.take<uint2>(n);
+    uint4 *d_tiles = V.take<uint4>(n);
     TileRef *d_ref = V.take<TileRef>(n);
     float *d_feat = V.take<float>(n * NFEAT);
     float *d_pred = V.take<float>(n);
     double *d64 = V.take<double>(n * TILE * 12);
     double *d32 = V.take<double>(n * TILE * 12);
     double *d_part = V.take<double>((size_t)pl.G * 3 * b->natom);
+    MolDesc *d_mol = V.take<MolDesc>(1);
     int launches = 0;
     std::vector<float> feat;
     rc = predict_tiles(b, pl, nullptr, pick, st, d_ref, d_feat, d_pred, nullptr, &feat, launches);
     if (rc != TG_OK) return rc;
+    const MolDesc md = make_desc(pl, 0);
+    TG_CUDA(cudaMemcpyAsync(d_mol, &md, sizeof(MolDesc), cudaMemcpyHostToDevice, st));
     // samples in class order so every launch covers a contiguous dump range
-    std::vector<std::vector<size_t>> lists(2 * NQC);
-    std::vector<size_t> order;  // position of each sample in the dump
+    std::vector<std::vector<size_t>> subset(1, pick);
     for (int r = 0; r < 2; ++r) {
-        for (auto &L : lists) L.clear();
-        for (size_t i : pick) lists[2 * pl.tiles[i].qc + r].push_back(i);
-        TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 3 * NQC, st));
-        TG_CUDA(cudaMemsetAsync(r ? d32 : d64, 0, sizeof(double) * n * TILE * 12, st));
-        rc = launch_lists(b, pl, lists, d_tiles, d_part, r ? d32 : d64, false, st, nullptr, launches);
+        std::vector<std::vector<uint8_t>> routes(1, std::vector<uint8_t>(pl.tiles.size(), (uint8_t)r));
+        Exec ex;
+        build_exec({&pl}, routes, &subset, ex);
+        ex.natom_total = ex.natom_max = b->natom;
+        TG_CUDA(cudaMemcpyAsync(d_tiles, ex.tiles.data(), sizeof(uint4) * ex.tiles.size(), cudaMemcpyHostToDevice, st));
+        TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 4 * NQC, st));
+        // the dump is written at list positions; lists are class-major with r fixed,
+        // so positions run over the samples in class order
+        rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, r ? d32 : d64, b->d_boys, pl.G, nullptr, false, st,
+                         nullptr, launches);
         if (rc != TG_OK) return rc;
         TG_CUDA(cudaStreamSynchronize(st));
     }
-    // dump position of sample k: class-major order of the lists
     std::vector<size_t> pos(pl.tiles.size(), 0);
     {
         size_t p = 0;
@@ -928,12 +1033,32 @@ int tg_tile_samples(const tg_basis *cb, int npair, const tg_pair *pairs, const t
     std::vector<double> h64(n * TILE * 12), h32(n * TILE * 12);
     TG_CUDA(cudaMemcpy(h64.data(), d64, sizeof(double) * h64.size(), cudaMemcpyDeviceToHost));
     TG_CUDA(cudaMemcpy(h32.data(), d32, sizeof(double) * h32.size(), cudaMemcpyDeviceToHost));
+    // a tile's contribution to the gradient: per atom and component, the sum
+    // over its quartets; target = the largest |sum| (fp64), err32 = the
+    // largest |sum(fp32) - sum(fp64)|
+    std::vector<double> s64(3 * (size_t)b->natom), s32(3 * (size_t)b->natom);
     for (size_t k = 0; k < n; ++k) {
+        const HostTile &t = pl.tiles[pick[k]];
+        const int P = pl.qc_P[t.qc], Qc = pl.qc_Q[t.qc];
+        std::fill(s64.begin(), s64.end(), 0.0);
+        std::fill(s32.begin(), s32.end(), 0.0);
         const size_t p = pos[pick[k]];
+        for (int q = 0; q < TILE; ++q) {
+            const int bi = t.bt * TB + q / TK, ki = t.kt * TK + q % TK;
+            if (bi >= (int)pl.cls[P].size() || ki >= (int)pl.cls[Qc].size()) continue;
+            const HostPair &u = pl.cls[P][bi], &v = pl.cls[Qc][ki];
+            const int at[4] = {b->sh_atom[u.sa], b->sh_atom[u.sb], b->sh_atom[v.sa], b->sh_atom[v.sb]};
+            const double *g64 = &h64[(p * TILE + q) * 12], *g32 = &h32[(p * TILE + q) * 12];
+            for (int X = 0; X < 4; ++X)
+                for (int i = 0; i < 3; ++i) {
+                    s64[at[X] * 3 + i] += g64[X * 3 + i];
+                    s32[at[X] * 3 + i] += g32[X * 3 + i];
+                }
+        }
         double mx = 0.0, me = 0.0;
-        for (size_t j = p * TILE * 12; j < (p + 1) * TILE * 12; ++j) {
-            mx = std::max(mx, std::fabs(h64[j]));
-            me = std::max(me, std::fabs(h64[j] - h32[j]));
+        for (size_t j = 0; j < s64.size(); ++j) {
+            mx = std::max(mx, std::fabs(s64[j]));
+            me = std::max(me, std::fabs(s32[j] - s64[j]));
         }
         target[k] = (float)std::log10(mx + 1e-30);
         err32[k] = (float)std::log10(me + 1e-30);
@@ -942,7 +1067,205 @@ int tg_tile_samples(const tg_basis *cb, int npair, const tg_pair *pairs, const t
     return TG_OK;
 }
 
+// ------------------------------------------------------------------ batch
+// Plan once, replay many: every molecule of the batch is planned (screening,
+// class sort, routing) at creation; one persistent launch per (class,
+// precision) then covers the tiles of all molecules, and the whole launch
+// sequence is captured in a CUDA graph that tg_batch_run replays.
+int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, const tg_pair *const *pairs,
+                    const tg_options *opt_in, tg_batch **out)
+{
+    if (!out || nmol < 1 || !bases || !npair || !pairs) return TG_EINVAL;
+    *out = nullptr;
+    tg_options opt;
+    if (opt_in) opt = *opt_in;
+    else tg_options_default(&opt);
+    if (opt.precision == TG_MIXED_LEARNED && (!opt.router || !opt.router->trained)) return TG_EROUTER;
+    for (int m = 0; m < nmol; ++m) {
+        if (!bases[m]) return TG_EINVAL;
+        for (int k = 0; k < m; ++k)
+            if (bases[k] == bases[m]) return TG_EINVAL;  // a basis holds one plan at a time
+    }
+    tg_batch *bt = new (std::nothrow) tg_batch();
+    if (!bt) return TG_ENOMEM;
+    std::unique_ptr<tg_batch, void (*)(tg_batch *)> guard(bt, [](tg_batch *x) { tg_batch_destroy(x); });
+    bt->nmol = nmol;
+    bt->plans.resize(nmol);
+    bt->device_ptrs = opt.device_ptrs;
+    cudaStream_t st = (cudaStream_t)opt.stream;
+    std::vector<std::vector<uint8_t>> routes(nmol);
+    std::vector<const Plan *> pp(nmol);
+    int natom_total = 0, natom_max = 0, G = 1;
+    for (int m = 0; m < nmol; ++m) {
+        tg_basis *b = const_cast<tg_basis *>(bases[m]);
+        bt->bases.push_back(b);
+        Plan &pl = bt->plans[m];
+        int rc = make_plan(b, npair[m], pairs[m], opt, st, pl);
+        if (rc != TG_OK) return rc;
+        bt->launches += pl.launches;
+        const size_t ntl = std::max<size_t>(pl.tiles.size(), 1);
+        DevArena &V = b->ws2;
+        TileRef *d_ref = V.take<TileRef>(ntl);
+        float *d_feat = V.take<float>(ntl * NFEAT);
+        float *d_pred = V.take<float>(ntl);
+        rc = compute_route(b, pl, opt, st, d_ref, d_feat, d_pred, routes[m], bt->launches);
+        if (rc != TG_OK) return rc;
+        bt->atom_off.push_back(natom_total);
+        natom_total += b->natom;
+        natom_max = std::max(natom_max, b->natom);
+        G = std::max(G, pl.G);
+        bt->pairs += pl.npairs_kept;
+        pp[m] = &pl;
+    }
+    build_exec(pp, routes, nullptr, bt->ex);
+    bt->ex.natom_total = natom_total;
+    bt->ex.natom_max = natom_max;
+    bt->G = G;
+    const size_t ntl = std::max<size_t>(bt->ex.tiles.size(), 1);
+    const size_t need = al(sizeof(MolDesc) * nmol) + al(sizeof(uint4) * ntl) +
+                        al(sizeof(double) * (size_t)G * 3 * natom_total) + al(sizeof(double) * 3 * natom_total) +
+                        al(sizeof(unsigned long long) * 4 * NQC) + 4096;
+    TG_CUDA(bt->arena.reserve(need));
+    bt->arena.used = 0;
+    bt->d_mols = bt->arena.take<MolDesc>(nmol);
+    bt->d_tiles = bt->arena.take<uint4>(ntl);
+    bt->d_part = bt->arena.take<double>((size_t)G * 3 * natom_total);
+    bt->d_grad = bt->arena.take<double>(3 * natom_total);
+    bt->d_cnt = bt->arena.take<unsigned long long>(4 * NQC);
+    std::vector<MolDesc> mds(nmol);
+    for (int m = 0; m < nmol; ++m) mds[m] = make_desc(bt->plans[m], bt->atom_off[m]);
+    TG_CUDA(cudaMemcpy(bt->d_mols, mds.data(), sizeof(MolDesc) * nmol, cudaMemcpyHostToDevice));
+    if (!bt->ex.tiles.empty())
+        TG_CUDA(cudaMemcpy(bt->d_tiles, bt->ex.tiles.data(), sizeof(uint4) * bt->ex.tiles.size(),
+                           cudaMemcpyHostToDevice));
+    const double *boys = bt->bases[0]->d_boys;
+
+    // ---- autotune the persistent grid of every (class, precision) list on a
+    // sample of its tiles: 1, 2, 3 or 4 CTAs per SM, fastest kept
+    bt->grids.assign(2 * NQC, G);
+    const int nsm = std::max(1, G / 2);
+    if (opt.reserved[0] == 1) {
+        cudaEvent_t e0, e1;
+        TG_CUDA(cudaEventCreate(&e0));
+        TG_CUDA(cudaEventCreate(&e1));
+        for (int k = 0; k < 2 * NQC; ++k) {
+            const long long nt = bt->ex.off[k + 1] - bt->ex.off[k];
+            if (nt <= nsm) continue;
+            Exec sub;
+            sub.natom_total = natom_total;
+            sub.natom_max = natom_max;
+            const long long ns = std::min<long long>(nt, 8LL * nsm);
+            for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : ns;
+            float best = 0.f;
+            for (int mult = 1; mult <= 4; ++mult) {
+                std::vector<int> gr(2 * NQC, mult * nsm);
+                int dummy = 0;
+                cudaEventRecord(e0, st);
+                int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt, nullptr,
+                                     boys, G, gr.data(), false, st, nullptr, dummy);
+                cudaEventRecord(e1, st);
+                if (rc != TG_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return rc;
+                }
+                TG_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (mult == 1 || ms < best) {
+                    best = ms;
+                    bt->grids[k] = mult * nsm;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        bt->G = G = std::max(G, *std::max_element(bt->grids.begin(), bt->grids.end()));
+    }
+    // the partial slabs must cover the largest tuned grid
+    if ((size_t)G * 3 * natom_total > (size_t)bt->plans[0].G * 3 * natom_total) {
+        // re-carve with the larger slab count
+        bt->arena.release();
+        const size_t need2 = al(sizeof(MolDesc) * nmol) + al(sizeof(uint4) * ntl) +
+                             al(sizeof(double) * (size_t)G * 3 * natom_total) + al(sizeof(double) * 3 * natom_total) +
+                             al(sizeof(unsigned long long) * 4 * NQC) + 4096;
+        TG_CUDA(bt->arena.reserve(need2));
+        bt->arena.used = 0;
+        bt->d_mols = bt->arena.take<MolDesc>(nmol);
+        bt->d_tiles = bt->arena.take<uint4>(ntl);
+        bt->d_part = bt->arena.take<double>((size_t)G * 3 * natom_total);
+        bt->d_grad = bt->arena.take<double>(3 * natom_total);
+        bt->d_cnt = bt->arena.take<unsigned long long>(4 * NQC);
+        TG_CUDA(cudaMemcpy(bt->d_mols, mds.data(), sizeof(MolDesc) * nmol, cudaMemcpyHostToDevice));
+        if (!bt->ex.tiles.empty())
+            TG_CUDA(cudaMemcpy(bt->d_tiles, bt->ex.tiles.data(), sizeof(uint4) * bt->ex.tiles.size(),
+                               cudaMemcpyHostToDevice));
+    }
+
+    // ---- capture the launch sequence once (a run first sets kernel attributes)
+    TG_CUDA(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking));
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) TG_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
+        int n = 0;
+        cudaMemsetAsync(bt->d_part, 0, sizeof(double) * (size_t)G * 3 * natom_total, bt->cap);
+        cudaMemsetAsync(bt->d_cnt, 0, sizeof(unsigned long long) * 4 * NQC, bt->cap);
+        int rc = launch_exec(bt->ex, bt->d_mols, bt->d_tiles, bt->d_part, bt->d_cnt, nullptr, boys, G,
+                             bt->grids.data(), false, bt->cap, nullptr, n);
+        k_reduce<<<(3 * natom_total + 127) / 128, 128, 0, bt->cap>>>(3 * natom_total, G, bt->d_part, bt->d_grad);
+        ++n;
+        if (pass == 1) {
+            cudaError_t e = cudaStreamEndCapture(bt->cap, &bt->graph);
+            if (rc != TG_OK) return rc;
+            TG_CUDA(e);
+            TG_CUDA(cudaGraphInstantiate(&bt->gexec, bt->graph, 0));
+            bt->launches = n;
+        } else {
+            if (rc != TG_OK) return rc;
+            TG_CUDA(cudaStreamSynchronize(bt->cap));
+        }
+    }
+    *out = guard.release();
+    return TG_OK;
+}
+
+int tg_batch_run(tg_batch *bt, double *const *grads, const tg_options *opt_in, tg_stats *stats)
+{
+    if (!bt || !grads) return TG_EINVAL;
+    auto t0 = std::chrono::steady_clock::now();
+    tg_options opt;
+    if (opt_in) opt = *opt_in;
+    else tg_options_default(&opt);
+    cudaStream_t st = (cudaStream_t)opt.stream;
+    TG_CUDA(cudaGraphLaunch(bt->gexec, st));
+    unsigned long long hc[4 * NQC];
+    TG_CUDA(cudaMemcpyAsync(hc, bt->d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    for (int m = 0; m < bt->nmol; ++m) {
+        if (!grads[m]) return TG_EINVAL;
+        TG_CUDA(cudaMemcpyAsync(grads[m], bt->d_grad + 3 * (size_t)bt->atom_off[m],
+                                sizeof(double) * 3 * bt->bases[m]->natom,
+                                opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    TG_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        fill_stats(stats, hc, bt->pairs, (long long)bt->ex.tiles.size(), bt->launches, bt->G);
+        for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return TG_OK;
+}
+
+void tg_batch_destroy(tg_batch *bt)
+{
+    if (!bt) return;
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
+    bt->arena.release();
+    delete bt;
+}
+
 }  // extern "C"
+
 
 // ------------------------------------------------------------------ router
 namespace {

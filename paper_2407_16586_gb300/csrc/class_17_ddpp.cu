@@ -3,11 +3,10 @@
 
 namespace tg {
 
-cudaError_t launch_qc17(int fp32, int grid, size_t smem, cudaStream_t st, const GeoArgs &geo, const DensArgs &den,
-                         const ScreenArgs &scr, const ClassLaunch &cl, const OutArgs &out, const PrimPairs &pp,
-                         const double *boys)
+cudaError_t launch_qc17(int fp32, int grid, size_t smem, cudaStream_t st, const MolDesc *mols,
+                         const ClassLaunch &cl, const OutArgs &out, const double *boys)
 {
-    return launch_class_kernel<2, 2, 1, 1>(fp32, grid, smem, st, geo, den, scr, cl, out, pp, boys);
+    return launch_class_kernel<2, 2, 1, 1>(fp32, grid, smem, st, mols, cl, out, boys);
 }
 
 }  // namespace tg

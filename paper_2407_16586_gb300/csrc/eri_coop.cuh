@@ -107,7 +107,10 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
         if (lane < 3) {
             const double P = lane == 0 ? Px : (lane == 1 ? Py : Pz);
             F E[LA + 2][LB + 1][L1 + 2];
-            etab<LA + 1, LB>(E, (F)(P - xa[lane]), (F)(P - xb[lane]), (F)(0.5 / p));
+            if constexpr (FP32)
+                etab<LA + 1, LB>(E, (F)pp.fPA[lane * pp.n + ip], (F)pp.fPB[lane * pp.n + ip], (F)(0.5f / pp.fp[ip]));
+            else
+                etab<LA + 1, LB>(E, (F)(P - xa[lane]), (F)(P - xb[lane]), (F)(0.5 / p));
             F *dst = Eb + lane * Lay::NEB;
             for (int i = 0; i <= LA + 1; ++i)
                 for (int j = 0; j <= LB; ++j)
@@ -173,12 +176,46 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
             if (lane < 3) {
                 const double Q = lane == 0 ? pp.Px[kp] : (lane == 1 ? pp.Py[kp] : pp.Pz[kp]);
                 F E[LC + 2][LD + 1][L2 + 2];
-                etab<LC + 1, LD>(E, (F)(Q - xc[lane]), (F)(Q - xd[lane]), (F)(0.5 / pp.p[kp]));
+                if constexpr (FP32)
+                    etab<LC + 1, LD>(E, (F)pp.fPA[lane * pp.n + kp], (F)pp.fPB[lane * pp.n + kp],
+                                     (F)(0.5f / pp.fp[kp]));
+                else
+                    etab<LC + 1, LD>(E, (F)(Q - xc[lane]), (F)(Q - xd[lane]), (F)(0.5 / pp.p[kp]));
                 F *dst = Ek + lane * Lay::NEK;
                 for (int i = 0; i <= LC + 1; ++i)
                     for (int j = 0; j <= LD; ++j)
                         for (int t = 0; t <= L2 + 1; ++t) dst[ebi(i, j, t, KJ, KT)] = E[i][j][t];
-            } else if (lane == 3 || (lane == 4 && lr)) {
+            } else if (FP32 && (lane == 3 || (lane == 4 && lr))) {
+                // fp32 scalars: P - Q = (P - A) - (Q - C) + (A - C)
+                const long long nr = pp.n;
+                const float pf = pp.fp[ip], qf = pp.fp[kp], pq = pf + qf, rho = pf * qf / pq;
+                const float X = pp.fPA[ip] - pp.fPA[kp] + (float)(xa[0] - xc[0]);
+                const float Y = pp.fPA[nr + ip] - pp.fPA[nr + kp] + (float)(xa[1] - xc[1]);
+                const float Z = pp.fPA[2 * nr + ip] - pp.fPA[2 * nr + kp] + (float)(xa[2] - xc[2]);
+                const float T = rho * (X * X + Y * Y + Z * Z);
+                const float pref = 34.986836655249725f * rsqrtf(pq) / (pf * qf) * pp.fK[ip] * pp.fK[kp];
+                const float om2f = (float)om2;
+                const float th2 = (lane == 3) ? 1.0f : (ominf ? 1.0f : om2f / (om2f + rho));
+                float Fm[L + 2];
+                boys_mixed<L + 1>(T * th2, Fm, boys);
+                F *base = Rb + (lane == 3 ? 2 : 3) * NR;
+                float f = pref * sqrtf(th2);
+                for (int n = 0; n <= L + 1; ++n) {
+                    base[n] = (F)((n & 1) ? -f * Fm[n] : f * Fm[n]);
+                    f *= th2;
+                }
+                if (lane == 3) {
+                    const float s = sqrtf(2.0f * rho);
+                    scl[0] = (F)(X * s);
+                    scl[1] = (F)(Y * s);
+                    scl[2] = (F)(Z * s);
+                    F pw = F(1);
+                    for (int n = 0; n <= L + 2; ++n) {
+                        scl[16 + n] = pw;
+                        pw *= (F)s;
+                    }
+                }
+            } else if (!FP32 && (lane == 3 || (lane == 4 && lr))) {
                 const double q = pp.p[kp], pq = p + q, rho = p * q / pq;
                 const double X = Px - pp.Px[kp], Y = Py - pp.Py[kp], Z = Pz - pp.Pz[kp];
                 const double T = rho * (X * X + Y * Y + Z * Z);
@@ -352,7 +389,8 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                             y += g0[hidx(t2, u2, v2)] * R[hr];
                             if (lr) y += g1[hidx(t2, u2, v2)] * Rl[hr];
                         }
-                YZ[it] = y * spow[n1];
+                if constexpr (FP32) y *= spow[n1];
+                YZ[it] = y;
             }
             group_sync(bar, GS);
             // d/dA and d/dP per bra component pair
@@ -422,11 +460,17 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                     for (int u1 = 0; u1 <= L1 - t1; ++u1)
                         for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
                             const int h1 = hidx(t1, u1, v1), hr = hidx(t1 + t2, u1 + u2, v1 + v2);
-                            const F sh = spow[t1 + u1 + v1];
-                            z += f0[h1] * sh * R[hr];
-                            if (lr) z += f1[h1] * sh * Rl[hr];
+                            if constexpr (FP32) {
+                                const F sh = spow[t1 + u1 + v1];
+                                z += f0[h1] * sh * R[hr];
+                                if (lr) z += f1[h1] * sh * Rl[hr];
+                            } else {
+                                z += f0[h1] * R[hr];
+                                if (lr) z += f1[h1] * Rl[hr];
+                            }
                         }
-                YZ[it] = (n2 & 1) ? -z * spow[n2] : z * spow[n2];
+                if constexpr (FP32) z *= spow[n2];
+                YZ[it] = (n2 & 1) ? -z : z;
             }
             group_sync(bar, GS);
             // d/dC per ket component pair
@@ -480,53 +524,72 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
 // takes quartets g, g + 128/GS, ... of every tile; the tile's 12 x TILE
 // contributions are then added in the same fixed order as k_grad.
 template <int LA, int LB, int LC, int LD, typename F, int GS>
-__global__ void __launch_bounds__(TILE) k_grad_coop(GeoArgs geo, DensArgs den, ScreenArgs scr, ClassLaunch cl,
-                                                    OutArgs out, PrimPairs pp, const double *__restrict__ boys)
+__global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ mols, ClassLaunch cl, OutArgs out,
+                                                    const double *__restrict__ boys)
 {
     using Lay = CoopLayout<LA, LB, LC, LD, F>;
     constexpr int NG = TILE / GS;
     extern __shared__ double smem[];
-    const int natom3 = geo.natom * 3;
-    double *sg = out.use_smem ? smem : out.partials + (size_t)blockIdx.x * natom3;
-    double *stg = smem + (out.use_smem ? natom3 : 0);
+    const int nacc3 = out.use_smem ? out.natom_max * 3 : 0;
+    double *sg = smem;
+    double *stg = smem + nacc3;
     int *sat = reinterpret_cast<int *>(stg + TILE * 12);
-    double *red = reinterpret_cast<double *>(sat + TILE * 4);  // [NG][GS/32][9]
+    double *tred = reinterpret_cast<double *>(sat + TILE * 4);
+    int *ratom = reinterpret_cast<int *>(tred + 6 * (TB + TK));
+    double *red = reinterpret_cast<double *>(ratom + 2 * (TB + TK));  // [NG][GS/32][9]
     F *gsm = reinterpret_cast<F *>(red + NG * (GS / 32) * 9) + (size_t)(threadIdx.x / GS) * Lay::TOTAL;
     const int grp = threadIdx.x / GS, lane = threadIdx.x % GS, bar = 1 + grp;
-    if (out.use_smem)
-        for (int k = threadIdx.x; k < natom3; k += blockDim.x) sg[k] = 0.0;
-    __syncthreads();
+    double *slab = out.partials + (size_t)blockIdx.x * out.natom_total * 3;
+    int cur = -1, cur_off3 = 0, cur_n3 = 0;
     unsigned long long nq = 0, npq = 0;
     for (long long it = blockIdx.x; it < cl.ntiles; it += gridDim.x) {
-        const uint2 tl = cl.tiles[it];
+        const uint4 tl = cl.tiles[it];
+        const int mol = (int)tl.x;
+        if (mol != cur) {
+            if (out.use_smem) {
+                if (cur >= 0)
+                    for (int k = threadIdx.x; k < cur_n3; k += blockDim.x) slab[cur_off3 + k] += sg[k];
+                __syncthreads();
+                for (int k = threadIdx.x; k < nacc3; k += blockDim.x) sg[k] = 0.0;
+                __syncthreads();
+            }
+            cur = mol;
+            cur_off3 = mols[mol].atom_off * 3;
+            cur_n3 = mols[mol].geo.natom * 3;
+        }
+        const MolDesc &md = mols[mol];
+        const PairSet bra = md.sets[cl.P], ket = md.sets[cl.Q];
+        const GeoArgs geo = md.geo;
+        const PrimPairs pp = md.pp;
+        const ScreenArgs scr = md.scr;
+        const bool same = cl.P == cl.Q;
         for (int qi = grp; qi < TILE; qi += NG) {
-            const int bi = tl.x * TB + qi / TK;
-            const int ki = tl.y * TK + qi % TK;
+            const int bi = tl.y * TB + qi / TK;
+            const int ki = tl.z * TK + qi % TK;
             double g[12];
 #pragma unroll
             for (int k = 0; k < 12; ++k) g[k] = 0.0;
             int at[4] = {-1, -1, -1, -1};
-            bool ok = bi < cl.bra.n && ki < cl.ket.n && (!cl.same || bi >= ki);
+            bool ok = bi < bra.n && ki < ket.n && (!same || bi >= ki);
             int sa = 0, sb = 0, sc = 0, sd = 0;
             if (ok) {
-                sa = cl.bra.sa[bi];
-                sb = cl.bra.sb[bi];
-                sc = cl.ket.sa[ki];
-                sd = cl.ket.sb[ki];
-                ok = keep_quartet(scr, cl.bra, cl.ket, bi, ki, sa, sb, sc, sd);
+                sa = bra.sa[bi];
+                sb = bra.sb[bi];
+                sc = ket.sa[ki];
+                sd = ket.sb[ki];
+                ok = keep_quartet(scr, bra, ket, bi, ki, sa, sb, sc, sd);
             }
             if (ok) {  // uniform across the group
                 double scale = 1.0;
                 if (sa == sb) scale *= 0.5;
                 if (sc == sd) scale *= 0.5;
-                if (cl.same && bi == ki) scale *= 0.5;
-                const int nbp = cl.bra.np[bi], nkp = cl.ket.np[ki];
+                if (same && bi == ki) scale *= 0.5;
+                const int nbp = bra.np[bi], nkp = ket.np[ki];
                 double acc[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) acc[k] = 0.0;
-                quartet_coop<LA, LB, LC, LD, F, GS>(gsm, lane, bar, geo, den, pp, sa, sb, sc, sd, cl.bra.poff[bi],
-                                                    nbp, cl.ket.poff[ki], nkp, scale, boys, acc);
-                // reduce the 9 partial sums over the group (fixed order)
+                quartet_coop<LA, LB, LC, LD, F, GS>(gsm, lane, bar, geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi],
+                                                    nbp, ket.poff[ki], nkp, scale, boys, acc);
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
 #pragma unroll
@@ -574,21 +637,11 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(GeoArgs geo, DensArgs den, S
             }
         }
         __syncthreads();
-        if (!out.dump && threadIdx.x < 3) {
-            const int i = threadIdx.x;
-            for (int t = 0; t < TILE; ++t)
-#pragma unroll
-                for (int X = 0; X < 4; ++X) {
-                    const int a = sat[t * 4 + X];
-                    if (a >= 0) sg[a * 3 + i] += stg[t * 12 + X * 3 + i];
-                }
-        }
+        if (!out.dump) tile_reduce(stg, sat, tred, ratom, out.use_smem ? sg : slab + cur_off3);
         __syncthreads();
     }
-    if (out.use_smem) {
-        double *dst = out.partials + (size_t)blockIdx.x * natom3;
-        for (int k = threadIdx.x; k < natom3; k += blockDim.x) dst[k] += sg[k];
-    }
+    if (out.use_smem && cur >= 0)
+        for (int k = threadIdx.x; k < cur_n3; k += blockDim.x) slab[cur_off3 + k] += sg[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         nq += __shfl_xor_sync(0xffffffffu, nq, o);
@@ -596,7 +649,7 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(GeoArgs geo, DensArgs den, S
     }
     if ((threadIdx.x & 31) == 0 && nq) {
         atomicAdd(out.counters + 0, nq);
-        atomicAdd(out.counters + 1, npq);
+        atomicAdd(out.counters + (sizeof(F) == 4 ? 3 : 1), npq);
         if (sizeof(F) == 4) atomicAdd(out.counters + 2, nq);
     }
 }
@@ -608,7 +661,7 @@ struct CoopChoice {
     static constexpr int work = Lay::NAB * Lay::NH1P > Lay::NCD * Lay::NH2P ? Lay::NAB * Lay::NH1P : Lay::NCD * Lay::NH2P;
     static constexpr int GS = work >= 1024 ? 128 : (work >= 320 ? 64 : 32);
     static constexpr size_t group_bytes() { return Lay::bytes(); }
-    static constexpr size_t bytes_all() { return (size_t)(TILE / GS) * Lay::bytes() + sizeof(double) * (TILE / GS) * (GS / 32) * 9; }
+    static constexpr size_t bytes_all() { return (size_t)(TILE / GS) * Lay::bytes() + sizeof(double) * (TILE / GS) * (GS / 32) * 9 + 64; }
 };
 
 }  // namespace tg
@@ -617,13 +670,14 @@ namespace tg {
 
 template <int LA, int LB, int LC, int LD>
 struct UseCoop {
-    static constexpr bool value = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD) >= 100;
+    // measured on the 32-atom workload: the cooperative form wins only for the
+    // two largest classes, (dd|dp) and (dd|dd)
+    static constexpr bool value = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD) >= 648;
 };
 
 template <int LA, int LB, int LC, int LD>
-cudaError_t launch_class_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const GeoArgs &geo,
-                                const DensArgs &den, const ScreenArgs &scr, const ClassLaunch &cl, const OutArgs &out,
-                                const PrimPairs &pp, const double *boys)
+cudaError_t launch_class_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const MolDesc *mols,
+                                const ClassLaunch &cl, const OutArgs &out, const double *boys)
 {
     if constexpr (UseCoop<LA, LB, LC, LD>::value) {
         cudaError_t e;
@@ -633,18 +687,18 @@ cudaError_t launch_class_kernel(int fp32, int grid, size_t smem, cudaStream_t st
             const size_t sm = smem + C::bytes_all();
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
-            kern<<<grid, TILE, sm, st>>>(geo, den, scr, cl, out, pp, boys);
+            kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
         } else {
             using C = CoopChoice<LA, LB, LC, LD, double>;
             auto kern = k_grad_coop<LA, LB, LC, LD, double, C::GS>;
             const size_t sm = smem + C::bytes_all();
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
-            kern<<<grid, TILE, sm, st>>>(geo, den, scr, cl, out, pp, boys);
+            kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
         }
         return cudaGetLastError();
     } else {
-        return launch_thread_kernel<LA, LB, LC, LD>(fp32, grid, smem, st, geo, den, scr, cl, out, pp, boys);
+        return launch_thread_kernel<LA, LB, LC, LD>(fp32, grid, smem, st, mols, cl, out, boys);
     }
 }
 

@@ -397,27 +397,27 @@ __device__ void quartet_fp64(const GeoArgs &geo, const DensArgs &den, const Prim
     }
 }
 
-// fp32 Boys function F_m(T), m = 0..M: same Taylor table (read in fp64 and
-// rounded) and downward recursion in fp32 for T >= 1; for T < 1 the fp64
-// routine is used.  Relative accuracy ~1e-7.
+// fp32 Boys function F_m(T), m = 0..M: fp32 Taylor table and downward
+// recursion for T >= 1; below T = 1 the fp64 routine is used.  Relative
+// accuracy ~1e-7.
 template <int M>
-__device__ __forceinline__ void boys_mixed(double Td, float (&F)[M + 1], const double *__restrict__ tab)
+__device__ __forceinline__ void boys_mixed(float T, float (&F)[M + 1], const double *__restrict__ tab)
 {
-    if (Td < 1.0) {
+    if (T < 1.0f) {
         double Fd[M + 1];
-        boys_fp64<M>(Td, Fd, tab);
+        boys_fp64<M>((double)T, Fd, tab);
 #pragma unroll
         for (int m = 0; m <= M; ++m) F[m] = (float)Fd[m];
         return;
     }
-    const float T = (float)Td;
-    if (Td < BOYS_TMAX) {
+    if (T < (float)BOYS_TMAX) {
+        const float *ftab = reinterpret_cast<const float *>(tab + BOYS_TAB);
         const int i = __float2int_rn(T * (float)(1.0 / BOYS_H));
-        const float d = (float)(i * BOYS_H - Td);
-        const double *row = tab + i * (BOYS_M + 1) + M;
-        float acc = (float)row[BOYS_TAYLOR];
+        const float d = (float)i * (float)BOYS_H - T;
+        const float *row = ftab + i * (BOYS_M + 1) + M;
+        float acc = row[BOYS_TAYLOR];
 #pragma unroll
-        for (int k = BOYS_TAYLOR - 1; k >= 0; --k) acc = (float)row[k] + acc * d * (1.0f / (k + 1));
+        for (int k = BOYS_TAYLOR - 1; k >= 0; --k) acc = row[k] + acc * d * (1.0f / (k + 1));
         F[M] = acc;
         const float et = __expf(-T);
         const float t2 = 2.0f * T;
@@ -465,20 +465,23 @@ __device__ void quartet_fp32(const GeoArgs &geo, const DensArgs &den, const Prim
     const double om2 = den.omega * den.omega;
     const bool ominf = isinf(den.omega);
 
-    const double *xa = geo.xyz + 3 * geo.sh_atom[sa], *xb = geo.xyz + 3 * geo.sh_atom[sb];
-    const double *xc = geo.xyz + 3 * geo.sh_atom[sc], *xd = geo.xyz + 3 * geo.sh_atom[sd];
+    const double *xa = geo.xyz + 3 * geo.sh_atom[sa], *xc = geo.xyz + 3 * geo.sh_atom[sc];
+    const float ACx = (float)(xa[0] - xc[0]), ACy = (float)(xa[1] - xc[1]), ACz = (float)(xa[2] - xc[2]);
+    const float om2f = (float)om2;
 
     double gA[3] = {0, 0, 0}, gC[3] = {0, 0, 0}, gT[3] = {0, 0, 0};
 
     for (int ib = 0; ib < nbp; ++ib) {
         const int ip = pb0 + ib;
-        const double p = pp.p[ip], Px = pp.Px[ip], Py = pp.Py[ip], Pz = pp.Pz[ip], Kab = pp.K[ip];
+        const long long nr = pp.n;
+        const float pf = pp.fp[ip], Kab = pp.fK[ip];
+        const float PAx = pp.fPA[ip], PAy = pp.fPA[nr + ip], PAz = pp.fPA[2 * nr + ip];
         const float za2 = 2.0f * pp.fza[ip];
-        const float oo2p = (float)(0.5 / p);
+        const float oo2p = 0.5f / pf;
         float Ebx[LA + 2][LB + 1][L1 + 2], Eby[LA + 2][LB + 1][L1 + 2], Ebz[LA + 2][LB + 1][L1 + 2];
-        etab<LA + 1, LB>(Ebx, (float)(Px - xa[0]), (float)(Px - xb[0]), oo2p);
-        etab<LA + 1, LB>(Eby, (float)(Py - xa[1]), (float)(Py - xb[1]), oo2p);
-        etab<LA + 1, LB>(Ebz, (float)(Pz - xa[2]), (float)(Pz - xb[2]), oo2p);
+        etab<LA + 1, LB>(Ebx, PAx, pp.fPB[ip], oo2p);
+        etab<LA + 1, LB>(Eby, PAy, pp.fPB[nr + ip], oo2p);
+        etab<LA + 1, LB>(Ebz, PAz, pp.fPB[2 * nr + ip], oo2p);
 
         float Fa[NCD][NH1], Fl[NCD][NH1];
 #pragma unroll
@@ -509,20 +512,22 @@ __device__ void quartet_fp32(const GeoArgs &geo, const DensArgs &den, const Prim
         float fA[3] = {0.f, 0.f, 0.f}, fC[3] = {0.f, 0.f, 0.f}, fT[3] = {0.f, 0.f, 0.f};
         for (int jk = 0; jk < nkp; ++jk) {
             const int kp = pk0 + jk;
-            const double q = pp.p[kp], Qx = pp.Px[kp], Qy = pp.Py[kp], Qz = pp.Pz[kp], Kcd = pp.K[kp];
+            const float qf = pp.fp[kp], Kcd = pp.fK[kp];
+            const float QCx = pp.fPA[kp], QCy = pp.fPA[nr + kp], QCz = pp.fPA[2 * nr + kp];
             const float zc2 = 2.0f * pp.fza[kp];
-            const float oo2q = (float)(0.5 / q);
+            const float oo2q = 0.5f / qf;
             float Ekx[LC + 2][LD + 1][L2 + 2], Eky[LC + 2][LD + 1][L2 + 2], Ekz[LC + 2][LD + 1][L2 + 2];
-            etab<LC + 1, LD>(Ekx, (float)(Qx - xc[0]), (float)(Qx - xd[0]), oo2q);
-            etab<LC + 1, LD>(Eky, (float)(Qy - xc[1]), (float)(Qy - xd[1]), oo2q);
-            etab<LC + 1, LD>(Ekz, (float)(Qz - xc[2]), (float)(Qz - xd[2]), oo2q);
+            etab<LC + 1, LD>(Ekx, QCx, pp.fPB[kp], oo2q);
+            etab<LC + 1, LD>(Eky, QCy, pp.fPB[nr + kp], oo2q);
+            etab<LC + 1, LD>(Ekz, QCz, pp.fPB[2 * nr + kp], oo2q);
 
-            const double pq = p + q;
-            const double rho = p * q / pq;
-            const double Xd = Px - Qx, Yd = Py - Qy, Zd = Pz - Qz;
-            const double T = rho * (Xd * Xd + Yd * Yd + Zd * Zd);
-            const float sc_ = (float)sqrt(2.0 * rho);
-            const float pref = (float)(34.986836655249725 / (p * q * sqrt(pq)) * Kab * Kcd);
+            // P - Q = (P - A) - (Q - C) + (A - C), all terms small
+            const float pq = pf + qf;
+            const float rho = pf * qf / pq;
+            const float Xd = PAx - QCx + ACx, Yd = PAy - QCy + ACy, Zd = PAz - QCz + ACz;
+            const float T = rho * (Xd * Xd + Yd * Yd + Zd * Zd);
+            const float sc_ = sqrtf(2.0f * rho);
+            const float pref = 34.986836655249725f * rsqrtf(pq) / (pf * qf) * Kab * Kcd;
             float spow[L + 3];
             spow[0] = 1.0f;
 #pragma unroll
@@ -535,10 +540,10 @@ __device__ void quartet_fp32(const GeoArgs &geo, const DensArgs &den, const Prim
                 for (int n = 0; n <= L + 1; ++n) base[n] = (n & 1) ? -pref * Fm[n] : pref * Fm[n];
                 hermite_R<L + 1>(R, base, (float)Xd * sc_, (float)Yd * sc_, (float)Zd * sc_);
                 if (lr) {
-                    const double th2 = ominf ? 1.0 : om2 / (om2 + rho);
+                    const float th2 = ominf ? 1.0f : om2f / (om2f + rho);
                     boys_mixed<L + 1>(T * th2, Fm, boys);
-                    float f = pref * (float)sqrt(th2);
-                    const float t2 = (float)th2;
+                    float f = pref * sqrtf(th2);
+                    const float t2 = th2;
 #pragma unroll
                     for (int n = 0; n <= L + 1; ++n) {
                         base[n] = (n & 1) ? -f * Fm[n] : f * Fm[n];
@@ -754,6 +759,300 @@ __device__ void quartet_fp32(const GeoArgs &geo, const DensArgs &den, const Prim
     }
 }
 
+// fp32 quartet, register-resident form.  Same algebra and scaled Hermite
+// basis as quartet_fp32, organised so the R tensor, the G row, y and z of
+// the current component pair stay in registers: the two operators are
+// processed one after the other (one R tensor live at a time), the Hermite
+// loops are fully unrolled, and only Gamma / F / E3k rows are read from
+// per-thread local memory (one load per row element).  The derivative dot
+// products use 1-D rows of the current component pair, zero beyond range.
+template <int LA, int LB, int LC, int LD>
+__device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp, int sa, int sb, int sc,
+                              int sd, int pb0, int nbp, int pk0, int nkp, double scale, const double *boys,
+                              double (&g)[12])
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int NAB = NA * NB, NCD = NC * ND;
+    constexpr int L1 = LA + LB, L2 = LC + LD, L = L1 + L2;
+    constexpr int NH1 = nherm(L1), NH1P = nherm(L1 + 1), NH2 = nherm(L2), NH2P = nherm(L2 + 1);
+    constexpr int NR = nherm(L + 1);
+    constexpr int E1 = L1 + 2, E2 = L2 + 2;  // 1-D row lengths
+
+    float gamf[2][NAB * NCD];
+    {
+        double gd[NAB * NCD], gdl[NAB * NCD];
+        build_gamma<LA, LB, LC, LD>(den, geo.sh_bf[sa], geo.sh_bf[sb], geo.sh_bf[sc], geo.sh_bf[sd], scale, gd, gdl);
+        for (int k = 0; k < NAB * NCD; ++k) {
+            gamf[0][k] = (float)gd[k];
+            gamf[1][k] = (float)gdl[k];
+        }
+    }
+    const int nops = den.use_lr ? 2 : 1;
+    const float om2f = (float)(den.omega * den.omega);
+    const bool ominf = isinf(den.omega);
+    const double *xa = geo.xyz + 3 * geo.sh_atom[sa], *xc = geo.xyz + 3 * geo.sh_atom[sc];
+    const float ACx = (float)(xa[0] - xc[0]), ACy = (float)(xa[1] - xc[1]), ACz = (float)(xa[2] - xc[2]);
+    const long long nr = pp.n;
+    double gA[3] = {0, 0, 0}, gC[3] = {0, 0, 0}, gT[3] = {0, 0, 0};
+
+    for (int ib = 0; ib < nbp; ++ib) {
+        const int ip = pb0 + ib;
+        const float pf = pp.fp[ip], Kab = pp.fK[ip];
+        const float PAx = pp.fPA[ip], PAy = pp.fPA[nr + ip], PAz = pp.fPA[2 * nr + ip];
+        const float za2 = 2.0f * pp.fza[ip];
+        // bra 1-D tables and component rows (local memory: indexed by component)
+        float Eb[3][LA + 2][LB + 1][L1 + 2];
+        etab<LA + 1, LB>(Eb[0], PAx, pp.fPB[ip], 0.5f / pf);
+        etab<LA + 1, LB>(Eb[1], PAy, pp.fPB[nr + ip], 0.5f / pf);
+        etab<LA + 1, LB>(Eb[2], PAz, pp.fPB[2 * nr + ip], 0.5f / pf);
+        // F_op[cd][h1] = sum_ab Gamma_op[ab][cd] E^{ab}_{h1}
+        float Fr[2][NCD][NH1];
+        for (int o = 0; o < nops; ++o)
+            for (int k = 0; k < NCD; ++k)
+#pragma unroll
+                for (int h = 0; h < NH1; ++h) Fr[o][k][h] = 0.0f;
+        for (int ab = 0; ab < NAB; ++ab) {
+            const int ma = ab / NB, mb = ab % NB;
+            const int aq = (ma == 0) ? 0 : (ma < 3 ? 1 : 2), bq = (mb == 0) ? 0 : (mb < 3 ? 1 : 2);
+            const int ay = aq - (ma - aq * (aq + 1) / 2), ax = LA - aq, az = LA - ax - ay;
+            const int by = bq - (mb - bq * (bq + 1) / 2), bx = LB - bq, bz = LB - bx - by;
+            float ex[E1], ey[E1], ez[E1];
+#pragma unroll
+            for (int t = 0; t < E1; ++t) {
+                ex[t] = t <= ax + bx ? Eb[0][ax][bx][t] : 0.0f;
+                ey[t] = t <= ay + by ? Eb[1][ay][by][t] : 0.0f;
+                ez[t] = t <= az + bz ? Eb[2][az][bz][t] : 0.0f;
+            }
+            float e3[NH1];
+#pragma unroll
+            for (int t = 0; t <= L1; ++t)
+#pragma unroll
+                for (int u = 0; u <= L1 - t; ++u)
+#pragma unroll
+                    for (int v = 0; v <= L1 - t - u; ++v) e3[hidx(t, u, v)] = ex[t] * ey[u] * ez[v];
+            for (int o = 0; o < nops; ++o)
+                for (int k = 0; k < NCD; ++k) {
+                    const float gm = gamf[o][ab * NCD + k];
+#pragma unroll
+                    for (int h = 0; h < NH1; ++h) Fr[o][k][h] += gm * e3[h];
+                }
+        }
+
+        float fA[3] = {0.f, 0.f, 0.f}, fC[3] = {0.f, 0.f, 0.f}, fT[3] = {0.f, 0.f, 0.f};
+        for (int jk = 0; jk < nkp; ++jk) {
+            const int kp = pk0 + jk;
+            const float qf = pp.fp[kp], Kcd = pp.fK[kp];
+            const float QCx = pp.fPA[kp], QCy = pp.fPA[nr + kp], QCz = pp.fPA[2 * nr + kp];
+            const float zc2 = 2.0f * pp.fza[kp];
+            float Ek[3][LC + 2][LD + 1][L2 + 2];
+            etab<LC + 1, LD>(Ek[0], QCx, pp.fPB[kp], 0.5f / qf);
+            etab<LC + 1, LD>(Ek[1], QCy, pp.fPB[nr + kp], 0.5f / qf);
+            etab<LC + 1, LD>(Ek[2], QCz, pp.fPB[2 * nr + kp], 0.5f / qf);
+            const float pq = pf + qf, rho = pf * qf / pq;
+            const float Xd = PAx - QCx + ACx, Yd = PAy - QCy + ACy, Zd = PAz - QCz + ACz;
+            const float T = rho * (Xd * Xd + Yd * Yd + Zd * Zd);
+            const float sc_ = sqrtf(2.0f * rho);
+            const float pref = 34.986836655249725f * rsqrtf(pq) / (pf * qf) * Kab * Kcd;
+            float spow[L + 3];
+            spow[0] = 1.0f;
+#pragma unroll
+            for (int n = 1; n <= L + 2; ++n) spow[n] = spow[n - 1] * sc_;
+            // ket products E^{cd}_{h2} s^{|h2|} (-1)^{|h2|}
+            float E3k[NCD][NH2];
+            for (int cd = 0; cd < NCD; ++cd) {
+                const int mc = cd / ND, md = cd % ND;
+                const int cq = (mc == 0) ? 0 : (mc < 3 ? 1 : 2), dq = (md == 0) ? 0 : (md < 3 ? 1 : 2);
+                const int cy = cq - (mc - cq * (cq + 1) / 2), cx = LC - cq, cz = LC - cx - cy;
+                const int dy = dq - (md - dq * (dq + 1) / 2), dx = LD - dq, dz = LD - dx - dy;
+                float kx[E2], ky[E2], kz[E2];
+#pragma unroll
+                for (int t = 0; t < E2; ++t) {
+                    kx[t] = t <= cx + dx ? Ek[0][cx][dx][t] : 0.0f;
+                    ky[t] = t <= cy + dy ? Ek[1][cy][dy][t] : 0.0f;
+                    kz[t] = t <= cz + dz ? Ek[2][cz][dz][t] : 0.0f;
+                }
+#pragma unroll
+                for (int t = 0; t <= L2; ++t)
+#pragma unroll
+                    for (int u = 0; u <= L2 - t; ++u)
+#pragma unroll
+                        for (int v = 0; v <= L2 - t - u; ++v) {
+                            const float w = ((t + u + v) & 1) ? -spow[t + u + v] : spow[t + u + v];
+                            E3k[cd][hidx(t, u, v)] = kx[t] * ky[u] * kz[v] * w;
+                        }
+            }
+            for (int o = 0; o < nops; ++o) {
+                float R[NR];
+                {
+                    const float th2 = (o == 0) ? 1.0f : (ominf ? 1.0f : om2f / (om2f + rho));
+                    float Fm[L + 2], base[L + 2];
+                    boys_mixed<L + 1>(T * th2, Fm, boys);
+                    float f = pref * sqrtf(th2);
+#pragma unroll
+                    for (int n = 0; n <= L + 1; ++n) {
+                        base[n] = (n & 1) ? -f * Fm[n] : f * Fm[n];
+                        f *= th2;
+                    }
+                    hermite_R<L + 1>(R, base, Xd * sc_, Yd * sc_, Zd * sc_);
+                }
+                // ---- bra side: y^{ab} (registers), then d/dA and d/dP
+                for (int ab = 0; ab < NAB; ++ab) {
+                    float gr[NH2];
+#pragma unroll
+                    for (int h = 0; h < NH2; ++h) gr[h] = 0.0f;
+                    for (int k = 0; k < NCD; ++k) {
+                        const float gm = gamf[o][ab * NCD + k];
+#pragma unroll
+                        for (int h = 0; h < NH2; ++h) gr[h] += gm * E3k[k][h];
+                    }
+                    float y[NH1P];
+#pragma unroll
+                    for (int h = 0; h < NH1P; ++h) y[h] = 0.0f;
+#pragma unroll
+                    for (int t2 = 0; t2 <= L2; ++t2)
+#pragma unroll
+                        for (int u2 = 0; u2 <= L2 - t2; ++u2)
+#pragma unroll
+                            for (int v2 = 0; v2 <= L2 - t2 - u2; ++v2) {
+                                const float c0 = gr[hidx(t2, u2, v2)];
+#pragma unroll
+                                for (int t1 = 0; t1 <= L1 + 1; ++t1)
+#pragma unroll
+                                    for (int u1 = 0; u1 <= L1 + 1 - t1; ++u1)
+#pragma unroll
+                                        for (int v1 = 0; v1 <= L1 + 1 - t1 - u1; ++v1)
+                                            y[hidx(t1, u1, v1)] += c0 * R[hidx(t1 + t2, u1 + u2, v1 + v2)];
+                            }
+                    const int ma = ab / NB, mb = ab % NB;
+                    const int aq = (ma == 0) ? 0 : (ma < 3 ? 1 : 2), bq = (mb == 0) ? 0 : (mb < 3 ? 1 : 2);
+                    const int ay = aq - (ma - aq * (aq + 1) / 2), ax = LA - aq, az = LA - ax - ay;
+                    const int by = bq - (mb - bq * (bq + 1) / 2), bx = LB - bq, bz = LB - bx - by;
+                    // rows: plain E (zero beyond i+j) and derivative DA = 2a E^{i+1} - i E^{i-1}
+                    float ex[E1], ey[E1], ez[E1], dx[E1], dy[E1], dz[E1];
+#pragma unroll
+                    for (int t = 0; t < E1; ++t) {
+                        ex[t] = t <= ax + bx ? Eb[0][ax][bx][t] : 0.0f;
+                        ey[t] = t <= ay + by ? Eb[1][ay][by][t] : 0.0f;
+                        ez[t] = t <= az + bz ? Eb[2][az][bz][t] : 0.0f;
+                        dx[t] = za2 * Eb[0][ax + 1][bx][t] - (ax > 0 ? ax * Eb[0][ax - 1][bx][t] : 0.0f);
+                        dy[t] = za2 * Eb[1][ay + 1][by][t] - (ay > 0 ? ay * Eb[1][ay - 1][by][t] : 0.0f);
+                        dz[t] = za2 * Eb[2][az + 1][bz][t] - (az > 0 ? az * Eb[2][az - 1][bz][t] : 0.0f);
+                    }
+                    // y_{tuv} s^{t+u+v}, contracted: sum_v (e_z, d_z, shifted e_z) then u, then t
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f;
+#pragma unroll
+                    for (int t = 0; t <= L1 + 1; ++t) {
+                        float ux = 0.f, uy = 0.f, uz = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+#pragma unroll
+                        for (int u = 0; u <= L1 + 1 - t; ++u) {
+                            float sE = 0.f, sD = 0.f, sS = 0.f;
+#pragma unroll
+                            for (int v = 0; v <= L1 + 1 - t - u; ++v) {
+                                const float yy = y[hidx(t, u, v)] * spow[t + u + v];
+                                if (v < E1) {
+                                    sE += ez[v] * yy;
+                                    sD += dz[v] * yy;
+                                }
+                                if (v >= 1) sS += ez[v - 1] * yy;
+                            }
+                            ux += ey[u] * sE;  // -> d/dA_x (with dx[t]) and d/dP_x (t-1)
+                            uy += dy[u] * sE;  // -> d/dA_y
+                            uz += ey[u] * sD;  // -> d/dA_z
+                            vz += ey[u] * sS;  // -> d/dP_z
+                            if (u >= 1) vy += ey[u - 1] * sE;  // -> d/dP_y
+                        }
+                        a0 += dx[t] * ux;
+                        a1 += ex[t] * uy;
+                        a2 += ex[t] * uz;
+                        if (t >= 1) q0 += ex[t - 1] * ux;
+                        q1 += ex[t] * vy;
+                        q2 += ex[t] * vz;
+                    }
+                    fA[0] += a0;
+                    fA[1] += a1;
+                    fA[2] += a2;
+                    fT[0] += q0;
+                    fT[1] += q1;
+                    fT[2] += q2;
+                }
+                // ---- ket side: z^{cd} (registers), then d/dC
+                for (int cd = 0; cd < NCD; ++cd) {
+                    float z[NH2P];
+#pragma unroll
+                    for (int h = 0; h < NH2P; ++h) z[h] = 0.0f;
+#pragma unroll
+                    for (int t1 = 0; t1 <= L1; ++t1)
+#pragma unroll
+                        for (int u1 = 0; u1 <= L1 - t1; ++u1)
+#pragma unroll
+                            for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
+                                const float f0 = Fr[o][cd][hidx(t1, u1, v1)] * spow[t1 + u1 + v1];
+#pragma unroll
+                                for (int t2 = 0; t2 <= L2 + 1; ++t2)
+#pragma unroll
+                                    for (int u2 = 0; u2 <= L2 + 1 - t2; ++u2)
+#pragma unroll
+                                        for (int v2 = 0; v2 <= L2 + 1 - t2 - u2; ++v2)
+                                            z[hidx(t2, u2, v2)] += f0 * R[hidx(t1 + t2, u1 + u2, v1 + v2)];
+                            }
+                    const int mc = cd / ND, md = cd % ND;
+                    const int cq = (mc == 0) ? 0 : (mc < 3 ? 1 : 2), dq = (md == 0) ? 0 : (md < 3 ? 1 : 2);
+                    const int cy = cq - (mc - cq * (cq + 1) / 2), cx = LC - cq, cz = LC - cx - cy;
+                    const int dy_ = dq - (md - dq * (dq + 1) / 2), dx_ = LD - dq, dz_ = LD - dx_ - dy_;
+                    float kx[E2], ky[E2], kz[E2], jx[E2], jy[E2], jz[E2];
+#pragma unroll
+                    for (int t = 0; t < E2; ++t) {
+                        kx[t] = t <= cx + dx_ ? Ek[0][cx][dx_][t] : 0.0f;
+                        ky[t] = t <= cy + dy_ ? Ek[1][cy][dy_][t] : 0.0f;
+                        kz[t] = t <= cz + dz_ ? Ek[2][cz][dz_][t] : 0.0f;
+                        jx[t] = zc2 * Ek[0][cx + 1][dx_][t] - (cx > 0 ? cx * Ek[0][cx - 1][dx_][t] : 0.0f);
+                        jy[t] = zc2 * Ek[1][cy + 1][dy_][t] - (cy > 0 ? cy * Ek[1][cy - 1][dy_][t] : 0.0f);
+                        jz[t] = zc2 * Ek[2][cz + 1][dz_][t] - (cz > 0 ? cz * Ek[2][cz - 1][dz_][t] : 0.0f);
+                    }
+                    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+                    for (int t = 0; t <= L2 + 1; ++t) {
+                        float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+                        for (int u = 0; u <= L2 + 1 - t; ++u) {
+                            float sE = 0.f, sD = 0.f;
+#pragma unroll
+                            for (int v = 0; v <= L2 + 1 - t - u; ++v) {
+                                const int n = t + u + v;
+                                const float zz = (n & 1) ? -z[hidx(t, u, v)] * spow[n] : z[hidx(t, u, v)] * spow[n];
+                                sE += kz[v] * zz;
+                                sD += jz[v] * zz;
+                            }
+                            ux += ky[u] * sE;
+                            uy += jy[u] * sE;
+                            uz += ky[u] * sD;
+                        }
+                        c0 += jx[t] * ux;
+                        c1 += kx[t] * uy;
+                        c2 += kx[t] * uz;
+                    }
+                    fC[0] += c0;
+                    fC[1] += c1;
+                    fC[2] += c2;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            gA[i] += (double)fA[i];
+            gC[i] += (double)fC[i];
+            gT[i] += (double)fT[i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g[i] = gA[i];
+        g[3 + i] = gT[i] - gA[i];
+        g[6 + i] = gC[i];
+        g[9 + i] = -gT[i] - gC[i];
+    }
+}
+
 // Per-quartet screening bound (see tdgrad.h) and shard membership.
 __device__ __forceinline__ bool keep_quartet(const ScreenArgs &scr, const PairSet &bra, const PairSet &ket, int bi,
                                              int ki, int sa, int sb, int sc, int sd)
@@ -778,46 +1077,67 @@ __device__ __forceinline__ bool keep_quartet(const ScreenArgs &scr, const PairSe
     return true;
 }
 
-// Persistent class kernel: CTA c takes tiles c, c+G, c+2G, ... of its class;
-// every tile's 12 x TILE gradient contributions are added to the CTA's
-// partial gradient in a fixed order, so results are bitwise reproducible.
+// Persistent class kernel: CTA c takes tiles c, c+G, c+2G, ... of its class
+// (all molecules of a batch; tiles are grouped by molecule).  Every tile's
+// 12 x TILE gradient contributions are added to the CTA's partial gradient
+// of the current molecule in a fixed order; the partial is flushed to the
+// CTA's slab when the molecule changes, so results are bitwise reproducible.
 template <int LA, int LB, int LC, int LD, bool FP32>
-__global__ void __launch_bounds__(TILE) k_grad(GeoArgs geo, DensArgs den, ScreenArgs scr, ClassLaunch cl,
-                                               OutArgs out, PrimPairs pp, const double *__restrict__ boys)
+__global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols, ClassLaunch cl, OutArgs out,
+                                               const double *__restrict__ boys)
 {
     extern __shared__ double smem[];
-    const int natom3 = geo.natom * 3;
-    double *sg = out.use_smem ? smem : out.partials + (size_t)blockIdx.x * natom3;
-    double *stg = smem + (out.use_smem ? natom3 : 0);
+    const int nacc3 = out.use_smem ? out.natom_max * 3 : 0;
+    double *sg = smem;
+    double *stg = smem + nacc3;
     int *sat = reinterpret_cast<int *>(stg + TILE * 12);
-    if (out.use_smem) {
-        for (int k = threadIdx.x; k < natom3; k += blockDim.x) sg[k] = 0.0;
-    }
-    __syncthreads();
+    double *red = reinterpret_cast<double *>(sat + TILE * 4);
+    int *ratom = reinterpret_cast<int *>(red + 6 * (TB + TK));
+    double *slab = out.partials + (size_t)blockIdx.x * out.natom_total * 3;
+    int cur = -1, cur_off3 = 0, cur_n3 = 0;
     unsigned long long nq = 0, npq = 0;
     for (long long it = blockIdx.x; it < cl.ntiles; it += gridDim.x) {
-        const uint2 tl = cl.tiles[it];
-        const int bi = tl.x * TB + threadIdx.x / TK;
-        const int ki = tl.y * TK + threadIdx.x % TK;
+        const uint4 tl = cl.tiles[it];
+        const int mol = (int)tl.x;
+        if (mol != cur) {
+            if (out.use_smem) {
+                if (cur >= 0)
+                    for (int k = threadIdx.x; k < cur_n3; k += blockDim.x) slab[cur_off3 + k] += sg[k];
+                __syncthreads();
+                for (int k = threadIdx.x; k < nacc3; k += blockDim.x) sg[k] = 0.0;
+                __syncthreads();
+            }
+            cur = mol;
+            cur_off3 = mols[mol].atom_off * 3;
+            cur_n3 = mols[mol].geo.natom * 3;
+        }
+        const MolDesc &md = mols[mol];
+        const PairSet bra = md.sets[cl.P], ket = md.sets[cl.Q];
+        const GeoArgs geo = md.geo;
+        const PrimPairs pp = md.pp;
+        const ScreenArgs scr = md.scr;
+        const bool same = cl.P == cl.Q;
+        const int bi = tl.y * TB + threadIdx.x / TK;
+        const int ki = tl.z * TK + threadIdx.x % TK;
         double g[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) g[k] = 0.0;
         int at[4] = {-1, -1, -1, -1};
-        bool ok = bi < cl.bra.n && ki < cl.ket.n && (!cl.same || bi >= ki);
+        bool ok = bi < bra.n && ki < ket.n && (!same || bi >= ki);
         if (ok) {
-            const int sa = cl.bra.sa[bi], sb = cl.bra.sb[bi], sc = cl.ket.sa[ki], sd = cl.ket.sb[ki];
-            ok = keep_quartet(scr, cl.bra, cl.ket, bi, ki, sa, sb, sc, sd);
+            const int sa = bra.sa[bi], sb = bra.sb[bi], sc = ket.sa[ki], sd = ket.sb[ki];
+            ok = keep_quartet(scr, bra, ket, bi, ki, sa, sb, sc, sd);
             if (ok) {
                 double scale = 1.0;
                 if (sa == sb) scale *= 0.5;
                 if (sc == sd) scale *= 0.5;
-                if (cl.same && bi == ki) scale *= 0.5;
-                const int nbp = cl.bra.np[bi], nkp = cl.ket.np[ki];
+                if (same && bi == ki) scale *= 0.5;
+                const int nbp = bra.np[bi], nkp = ket.np[ki];
                 if constexpr (FP32)
-                    quartet_fp32<LA, LB, LC, LD>(geo, den, pp, sa, sb, sc, sd, cl.bra.poff[bi], nbp, cl.ket.poff[ki],
-                                                 nkp, scale, boys, g);
+                    quartet_fp32r<LA, LB, LC, LD>(geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi], nbp, ket.poff[ki],
+                                                  nkp, scale, boys, g);
                 else
-                    quartet_fp64<LA, LB, LC, LD>(geo, den, pp, sa, sb, sc, sd, cl.bra.poff[bi], nbp, cl.ket.poff[ki],
+                    quartet_fp64<LA, LB, LC, LD>(geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi], nbp, ket.poff[ki],
                                                  nkp, scale, boys, g);
                 at[0] = geo.sh_atom[sa];
                 at[1] = geo.sh_atom[sb];
@@ -838,21 +1158,11 @@ __global__ void __launch_bounds__(TILE) k_grad(GeoArgs geo, DensArgs den, Screen
 #pragma unroll
         for (int k = 0; k < 4; ++k) sat[threadIdx.x * 4 + k] = at[k];
         __syncthreads();
-        if (threadIdx.x < 3) {
-            const int i = threadIdx.x;
-            for (int t = 0; t < TILE; ++t)
-#pragma unroll
-                for (int X = 0; X < 4; ++X) {
-                    const int a = sat[t * 4 + X];
-                    if (a >= 0) sg[a * 3 + i] += stg[t * 12 + X * 3 + i];
-                }
-        }
+        tile_reduce(stg, sat, red, ratom, out.use_smem ? sg : slab + cur_off3);
         __syncthreads();
     }
-    if (out.use_smem) {
-        double *dst = out.partials + (size_t)blockIdx.x * natom3;
-        for (int k = threadIdx.x; k < natom3; k += blockDim.x) dst[k] += sg[k];
-    }
+    if (out.use_smem && cur >= 0)
+        for (int k = threadIdx.x; k < cur_n3; k += blockDim.x) slab[cur_off3 + k] += sg[k];
     // counters
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -861,20 +1171,19 @@ __global__ void __launch_bounds__(TILE) k_grad(GeoArgs geo, DensArgs den, Screen
     }
     if ((threadIdx.x & 31) == 0 && nq) {
         atomicAdd(out.counters + 0, nq);
-        atomicAdd(out.counters + 1, npq);
+        atomicAdd(out.counters + (FP32 ? 3 : 1), npq);
         if (FP32) atomicAdd(out.counters + 2, nq);
     }
 }
 
 template <int LA, int LB, int LC, int LD>
-cudaError_t launch_thread_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const GeoArgs &geo,
-                                const DensArgs &den, const ScreenArgs &scr, const ClassLaunch &cl, const OutArgs &out,
-                                const PrimPairs &pp, const double *boys)
+cudaError_t launch_thread_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const MolDesc *mols,
+                                 const ClassLaunch &cl, const OutArgs &out, const double *boys)
 {
     auto kern = fp32 ? k_grad<LA, LB, LC, LD, true> : k_grad<LA, LB, LC, LD, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, TILE, smem, st>>>(geo, den, scr, cl, out, pp, boys);
+    kern<<<grid, TILE, smem, st>>>(mols, cl, out, boys);
     return cudaGetLastError();
 }
 

@@ -21,10 +21,13 @@ __global__ void k_boys_table(double *tab)
     }
     const double et = exp(-T);
     double f = et * sum;
+    float *ftab = reinterpret_cast<float *>(tab + BOYS_TAB);
     tab[i * (BOYS_M + 1) + BOYS_M] = f;
+    ftab[i * (BOYS_M + 1) + BOYS_M] = (float)f;
     for (int m = BOYS_M; m > 0; --m) {
         f = (2.0 * T * f + et) / (2 * m - 1);
         tab[i * (BOYS_M + 1) + m - 1] = f;
+        ftab[i * (BOYS_M + 1) + m - 1] = (float)f;
     }
 }
 
@@ -279,7 +282,7 @@ __global__ void k_prim_pairs(int npairs, const int *psa, const int *psb, const i
                              const double *exps, const double *cn, const long long *bpoff, const double *bp,
                              double scale, double qq, double mmax, double eps_p, double *p_, double *Px, double *Py,
                              double *Pz, double *K, double *za_, float *fp, float *fPx, float *fPy, float *fPz,
-                             float *fK, float *fza)
+                             float *fK, float *fza, float *fPA, float *fPB, long long nrec)
 {
     const int ip = blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= npairs) return;
@@ -310,6 +313,12 @@ __global__ void k_prim_pairs(int npairs, const int *psa, const int *psb, const i
             fPz[o] = (float)pz;
             fK[o] = (float)k;
             fza[o] = (float)za;
+            fPA[o] = (float)(px - A[0]);
+            fPA[nrec + o] = (float)(py - A[1]);
+            fPA[2 * nrec + o] = (float)(pz - A[2]);
+            fPB[o] = (float)(px - B[0]);
+            fPB[nrec + o] = (float)(py - B[1]);
+            fPB[2 * nrec + o] = (float)(pz - B[2]);
             ++o;
         }
 }

@@ -20,7 +20,7 @@ __global__ void k_prim_pairs(int npairs, const int *psa, const int *psb, const i
                              const double *exps, const double *cn, const long long *bpoff, const double *bp,
                              double scale, double qq, double mmax, double eps_p, double *p_, double *Px, double *Py,
                              double *Pz, double *K, double *za_, float *fp, float *fPx, float *fPy, float *fPz,
-                             float *fK, float *fza);
+                             float *fK, float *fza, float *fPA, float *fPB, long long nrec);
 __global__ void k_symm(int nbf, const double *A, double *S);
 __global__ void k_reduce(int n, int nslab, const double *partials, double *grad);
 

@@ -20,6 +20,8 @@ constexpr int BOYS_NG = 721;
 constexpr double BOYS_H = 0.05;
 constexpr double BOYS_TMAX = 36.0;
 constexpr int BOYS_TAYLOR = 6;
+// the fp32 copy of the table follows the fp64 one in the same allocation
+constexpr int BOYS_TAB = BOYS_NG * (BOYS_M + 1);
 
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 // number of Hermite (or Cartesian) triples with total <= L
@@ -49,6 +51,8 @@ struct PairSet {
 struct PrimPairs {
     const double *p, *Px, *Py, *Pz, *K, *za;
     const float *fp, *fPx, *fPy, *fPz, *fK, *fza;  // fp32 mirrors
+    const float *fPA, *fPB;                        // fp32 P - A and P - B, [3][n] (x, y, z planes)
+    long long n;                                   // records (plane stride of fPA / fPB)
 };
 
 struct DensArgs {
@@ -74,20 +78,77 @@ struct ScreenArgs {
     int rank, nranks;
 };
 
+// Everything a class kernel needs about one molecule; kernels read it from
+// a device array indexed by the tile's molecule id.
+struct MolDesc {
+    GeoArgs geo;
+    DensArgs den;
+    ScreenArgs scr;
+    PrimPairs pp;
+    PairSet sets[NPC];
+    int atom_off;  // first atom of this molecule in the batch gradient
+    int pad;
+};
+
 struct ClassLaunch {
-    PairSet bra, ket;
-    int same;                  // bra and ket lists are the same pair class
+    int P, Q;                  // bra and ket pair classes (same list iff P == Q)
     long long ntiles;
-    const uint2 *tiles;        // (bra tile, ket tile)
-    const uint8_t *route;      // per tile: 0 fp64, 1 fp32 (nullable = all fp64)
+    const uint4 *tiles;        // (molecule, bra tile, ket tile, 0), grouped by molecule
 };
 
 struct OutArgs {
-    double *partials;                 // [gridDim][natom*3], accumulated
-    unsigned long long *counters;     // [0] quartets, [1] primitive quartets, [2] fp32 quartets
-    int use_smem;                     // partial gradient kept in shared memory
+    double *partials;                 // [gridDim][natom_total*3], accumulated
+    int natom_total;                  // atoms of the whole batch
+    int natom_max;                    // atoms of the largest molecule
+    unsigned long long *counters;     // [0] quartets, [1] fp64 primitive quartets, [2] fp32 quartets, [3] fp32 pq
+    int use_smem;                     // per-molecule partial gradient kept in shared memory
     double *dump;                     // nullable: per-quartet gradients [tile][TILE][12] instead of reducing
 };
+
+// Deterministic reduction of one staged tile into the per-molecule partial
+// gradient tgt[atom*3 + i].  stg[q*12 + X*3 + i] holds quartet q's gradient
+// on centre X (A, B, C, D); sat[q*4 + X] its atom (-1: quartet not computed).
+// Quartet q = b*TK + j has bra pair row b and ket pair column j, so the A/B
+// parts of a row and the C/D parts of a column share their atoms: rows and
+// columns are summed in parallel first, then three threads (one per
+// component) add the 2*TB + 2*TK sums in a fixed order.  red: 6*(TB+TK)
+// doubles and 2*(TB+TK) ints of scratch.  All TILE threads must call it.
+__device__ __forceinline__ void tile_reduce(const double *stg, const int *sat, double *red, int *ratom, double *tgt)
+{
+    const int t = threadIdx.x;
+    for (int w = t; w < 6 * (TB + TK); w += TILE) {
+        if (w < TB * 6) {  // row b, centre X in {A, B}, component i
+            const int b = w / 6, X = (w % 6) / 3, i = w % 3;
+            double s = 0.0;
+            int a = -1;
+            for (int j = 0; j < TK; ++j) {
+                const int q = b * TK + j;
+                s += stg[q * 12 + X * 3 + i];
+                if (a < 0) a = sat[q * 4 + X];
+            }
+            red[w] = s;
+            if (i == 0) ratom[b * 2 + X] = a;
+        } else {  // column j, centre X in {C, D}, component i
+            const int u = w - TB * 6, j = u / 6, X = 2 + (u % 6) / 3, i = u % 3;
+            double s = 0.0;
+            int a = -1;
+            for (int b = 0; b < TB; ++b) {
+                const int q = b * TK + j;
+                s += stg[q * 12 + X * 3 + i];
+                if (a < 0) a = sat[q * 4 + X];
+            }
+            red[w] = s;
+            if (i == 0) ratom[TB * 2 + j * 2 + (X - 2)] = a;
+        }
+    }
+    __syncthreads();
+    if (t < 3) {
+        for (int r = 0; r < 2 * (TB + TK); ++r) {
+            const int a = ratom[r];
+            if (a >= 0) tgt[a * 3 + t] += red[r * 3 + t];
+        }
+    }
+}
 
 // ---------------------------------------------------------------- Boys
 // F_m(T) for m = 0..M (M <= BOYS_M - BOYS_TAYLOR).  T < 36: Taylor expansion

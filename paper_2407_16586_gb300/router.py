@@ -4,14 +4,14 @@ Samples quartet tiles of seeded training clusters (fp64 and fp32 evaluation
 of the same tiles, no reduction), trains the MLP on the GPU, and calibrates
 two constants on held-out tiles:
 
-* margin: the 99.9th percentile of (log10 true magnitude - prediction), so the
-  routed estimate 10^(prediction + margin) is rarely below the truth;
-* eps_rel: the 99.9th percentile of the fp32 error of a tile relative to its
-  largest fp64 contribution.
+* margin: the 99th percentile of (log10 true contribution - prediction), so
+  10^(prediction + margin) is rarely below the tile's true contribution;
+* eps_rel: the 99th percentile of the fp32 error of a tile's contribution
+  relative to the contribution.
 
-TG_MIXED_LEARNED then sends a tile to fp32 only while the summed estimate
-eps_rel * 128 * 10^(prediction + margin) of all fp32 tiles stays within the
-call's mixed_tol (default 1e-6 Ha/bohr)."""
+TG_MIXED_LEARNED then sends tiles to fp32 in increasing order of
+e_t = eps_rel * 10^(prediction + margin) while sum e_t^2 <= (mixed_tol/3)^2
+(mixed_tol defaults to 1e-6 Ha/bohr)."""
 from __future__ import annotations
 
 import numpy as np
@@ -43,10 +43,10 @@ def fit(X, y, e, seed=7, epochs=400, lr=1e-2, q=0.9, holdout=0.2, floor=-20.0):
     r = tg.Router(seed=seed)
     hist = r.train(X[tr], y[tr], epochs=epochs, lr=lr, q=q)
     pred = r.predict(X[hold])
-    margin = float(max(0.0, np.quantile(y[hold] - pred, 0.999)))
-    rel = 10.0 ** (np.minimum(e, 0.0) - y)
+    margin = float(max(0.0, np.quantile(y[hold] - pred, 0.99)))
+    rel = 10.0 ** (e - y)
     keep = y > floor + 1
-    eps_rel = float(np.quantile(rel[keep], 0.999)) if keep.any() else 1e-5
+    eps_rel = float(np.quantile(rel[keep], 0.99)) if keep.any() else 1e-5
     r.set(calib=[margin, eps_rel, 1.0])
     info = dict(n_train=len(tr), n_hold=nh, loss_first=float(hist[0]), loss_last=float(hist[-1]), margin=margin,
                 eps_rel=eps_rel, resid_hold_mean=float(np.mean(y[hold] - pred)))

@@ -1,0 +1,51 @@
+"""Train the block router on seeded 30-80-atom clusters and write its weights.
+
+  python -m paper_2407_16586_gb300.train_router [--clusters 200] [--stride 40]
+         [--out paper_2407_16586_gb300/data/router.bin]
+
+Every cluster comes from synth.router_cluster(i) (seed 20240716 + i); every
+stride-th screened quartet tile of each is evaluated in fp64 and fp32
+(tg_tile_samples), the MLP is trained on the GPU (tg_router_train) and the
+margin / eps_rel calibration is taken on 20 % held-out tiles."""
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--clusters", type=int, default=200)
+    ap.add_argument("--first", type=int, default=0)
+    ap.add_argument("--stride", type=int, default=40)
+    ap.add_argument("--cap", type=int, default=20000)
+    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "router.bin"))
+    args = ap.parse_args()
+    from paper_2407_16586_gb300 import build
+    build.build()
+    import paper_2407_16586_gb300 as tg
+    from paper_2407_16586_gb300 import router, synth
+    t0 = time.time()
+    Xs, ys, es = [], [], []
+    for i in range(args.first, args.first + args.clusters):
+        s = synth.router_cluster(i)
+        X, y, e = router.collect([s], stride=args.stride, cap=args.cap)
+        Xs.append(X)
+        ys.append(y)
+        es.append(e)
+    X, y, e = np.concatenate(Xs), np.concatenate(ys), np.concatenate(es)
+    t1 = time.time()
+    r, info = router.fit(X, y, e, epochs=args.epochs)
+    r.save(args.out)
+    info.update(clusters=args.clusters, stride=args.stride, tiles=int(len(y)), sample_s=t1 - t0,
+                train_s=time.time() - t1)
+    with open(args.out + ".json", "w") as f:
+        json.dump(info, f, indent=1)
+    print(json.dumps(info))
+
+
+if __name__ == "__main__":
+    main()
