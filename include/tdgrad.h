@@ -189,6 +189,31 @@ int tg_router_train(tg_router *r, int n, const float *X, const float *y, int epo
 int tg_router_loss_grad(const tg_router *r, int n, const float *X, const float *y, float q, float *loss,
                         float *grad);
 int tg_router_predict(const tg_router *r, int n, const float *X, float *out);
+
+/* Allocation-free loss and gradient of router parameters, for callers that
+ * cannot call cudaMalloc or cudaFree where they need it: code running while
+ * a stream is captured into a CUDA graph (allocation calls are illegal in a
+ * global-mode capture), code sharing the device with a framework whose
+ * caching allocator holds the free memory, and latency-critical loops that
+ * cannot take the device synchronisation cudaFree may cause.  The paper has
+ * no counterpart.
+ * Every argument is a caller-owned DEVICE pointer on the current device: X
+ * (n*16 standardised-or-raw features), y (n), mu and sd (16 each), params
+ * (tg_router_nparam() floats, layout of tg_router_get), loss (1 float) and
+ * grad (tg_router_nparam() floats) receive the expectile loss (quantile q)
+ * and its gradient, as tg_router_loss_grad computes them.  stream: a
+ * cudaStream_t or NULL; the call is asynchronous on it.
+ * Scratch: a fixed 3.3 MB device array inside the library (per-block partial
+ * sums for n <= 65536; larger n returns TG_EUNSUPPORTED).  Every device that
+ * loads the library holds it until the process exits.  All calls on a device
+ * share it: calls that overlap on the GPU (different streams, or another
+ * host thread) race and must be serialised by the caller.  Every call
+ * rewrites the parts it reads, so nothing carries over between calls.
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress) and sets the kernel's shared-memory limit; make that
+ * first call before any stream capture. */
+int tg_router_loss_grad_noalloc(int n, const float *X, const float *y, const float *mu, const float *sd,
+                                const float *params, float q, float *loss, float *grad, void *stream);
 int tg_router_save(const tg_router *r, const char *path);
 int tg_router_load(const char *path, tg_router **out);
 
