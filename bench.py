@@ -110,6 +110,19 @@ def _peaks():
         return {}
 
 
+def aggregate_over_ranks(dist, ms, units, device):
+    """Whole-job view of one timed region: (max ms over ranks, units summed
+    over ranks).  Identity without a process group."""
+    if dist is None:
+        return ms, float(units)
+    import torch
+    t_max = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    t_sum = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_sum)
+    return float(t_max.item()), float(t_sum.item())
+
+
 def run_reference(args):
     """The fp64 CPU oracle on bounded shards of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -243,15 +256,7 @@ def main():
     total_ms, quartets, launches, st_last = timed(prec, args.steps)
     stop.set()
     th.join(timeout=2)
-    t_max = total_ms
-    quartets_all = float(quartets)
-    if dist:
-        t = torch.tensor([total_ms, float(quartets)], device=dev, dtype=torch.float64)
-        tt = t.clone()
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t)
-        t_max = float(tt[0].item())
-        quartets_all = float(t[1].item())
+    t_max, quartets_all = aggregate_over_ranks(dist, total_ms, quartets, dev)
     value = quartets_all / (t_max / 1e3)
 
     # end to end through the public API with host buffers (pinned)
@@ -268,11 +273,7 @@ def main():
                              stream=stream.cuda_stream)
         e2e_ms += 1e3 * (time.perf_counter() - t)
         e2e_q += st["quartets"]
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-        e2e_q *= world
+    e2e_ms, e2e_q = aggregate_over_ranks(dist, e2e_ms, e2e_q, dev)
     h2d = sum(a.nbytes + b.nbytes for (a, b, *_r) in hpairs)
     d2h = hout.nbytes
 
