@@ -123,15 +123,31 @@ def aggregate_over_ranks(dist, ms, units, device):
     return float(t_max.item()), float(t_sum.item())
 
 
+def workload(name):
+    """The timed system: "c2" (the default, the 32-atom chain), "c1" (6 atoms),
+    or "chain:SEED:NHEAVY:NH" (a smaller chain of the same recipe, used for
+    profiler captures)."""
+    from paper_2407_16586_gb300 import synth
+    if name == "c1":
+        return synth.config(0), "c1: 2 O + 4 H, 50 bf, 2 density pairs"
+    if name == "c2":
+        return synth.config(1), WORKLOAD
+    parts = name.split(":")
+    if len(parts) == 4 and parts[0] == "chain":
+        seed, nheavy, nh = (int(x) for x in parts[1:])
+        return synth.molecule(seed, nheavy, nh), "chain seed %d: %d heavy + %d H, same recipe as c2" % (
+            seed, nheavy, nh)
+    raise ValueError("unknown workload %r" % name)
+
+
 def run_reference(args):
     """The fp64 CPU oracle on bounded shards of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
-    from paper_2407_16586_gb300 import synth
     oracle.build()
-    s = synth.config(1)
+    s, wname = workload(args.workload)
     nshard = args.ref_shards
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     times, nqs = [], []
@@ -143,29 +159,27 @@ def run_reference(args):
             times.append(dt)
             nqs.append(nq)
     val = sum(nqs) / sum(times)
-    sample = "shards %d..%d of %d of the c2 quartet set (bra-pair key mod %d)" % (
-        args.warmup % nshard, (args.warmup + args.steps - 1) % nshard, nshard, nshard)
+    sample = "shards %d..%d of %d of the %s quartet set (pair key mod %d)" % (
+        args.warmup % nshard, (args.warmup + args.steps - 1) % nshard, nshard, args.workload, nshard)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "data": "synthetic", "config": {"workload": wname, "sample": sample},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def cpu_baseline(shards=600, shard=0):
+def cpu_baseline(s, name, shards=600, shard=0):
     import oracle
-    from paper_2407_16586_gb300 import synth
     oracle.build()
-    s = synth.config(1)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     t = time.perf_counter()
     _, _, nq = oracle.grad2e(s, tau=TAU, rank=shard, nranks=shards, nthreads=cores)
     dt = time.perf_counter() - t
     return {"value": nq / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "shard %d of %d of the c2 quartets (%d quartets, %.1f s)" % (shard, shards, nq, dt)}
+            "sample": "shard %d of %d of the %s quartets (%d quartets, %.1f s)" % (shard, shards, name, nq, dt)}
 
 
 def _flops_of(st, qc, fp32):
@@ -185,6 +199,7 @@ def main():
     ap.add_argument("--router", default=os.path.join(ROOT, "paper_2407_16586_gb300", "data", "router.bin"))
     ap.add_argument("--ref-shards", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", help='c2 (default), c1, or chain:SEED:NHEAVY:NH')
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -212,7 +227,7 @@ def main():
             "fp32": tg.TG_FP32}[args.precision]
     router = tg.Router(path=args.router) if prec == tg.TG_MIXED_LEARNED else None
 
-    s = synth.config(1)
+    s, wname = workload(args.workload)
     basis = tg.Basis(s)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -301,7 +316,10 @@ def main():
         la, lb, lc, ld = class_ls()[qc]
         achieved = flops / (ms / 1e3) / 1e12
         pk = peaks["fp32" if fp32 else "fp64"]
-        kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if (la, lb, lc, ld) in ((2, 2, 2, 2), (2, 2, 2, 1)) else "",
+        nc = lambda l: (l + 1) * (l + 2) // 2
+        nfq = nc(la) * nc(lb) * nc(lc) * nc(ld)
+        coop = nfq >= (648 if fp32 else 54)  # the library's kernel choice per class
+        kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if coop else "",
                                                names[la], names[lb], names[lc], names[ld],
                                                "fp32" if fp32 else "fp64")
         tot_flops = sum(_flops_of(st_t, q, f)[1] for q in range(21) for f in (False, True))
@@ -311,7 +329,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "screen_tol": TAU, "mixed_tol": 1e-6,
+            "config": {"workload": wname, "precision": args.precision, "screen_tol": TAU, "mixed_tol": 1e-6,
                        "quartets_per_step": st0["quartets"], "fp32_quartets_per_step": st0["fp32_quartets"],
                        "prim_quartets_per_step": st0["prim_quartets"], "pairs": st0["pairs"], "tiles": st0["tiles"],
                        "l2": "flushed (512 MB write) before each timed step",
@@ -329,7 +347,7 @@ def main():
         if fp64 is not None:
             line["fp64"] = fp64
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(shards=args.ref_shards)
+            line["cpu_baseline"] = cpu_baseline(s, args.workload, shards=args.ref_shards)
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

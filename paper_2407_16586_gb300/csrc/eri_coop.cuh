@@ -35,8 +35,10 @@ struct CoopLayout {
     static constexpr int o_gaml = o_gam + NAB * NCD;
     static constexpr int o_F = o_gaml + NAB * NCD;          // [2][NCD][NH1]
     static constexpr int o_E3k = o_F + 2 * NCD * NH1;       // [NCD][NH2]
-    static constexpr int o_R = o_E3k + NCD * NH2;           // [4][NR] (R, Rl, ping-pong copies)
-    static constexpr int o_G = o_R + 4 * NR;                // [2][NAB][NH2]; E3b [NAB][NH1] aliases it
+    static constexpr int S = L + 2;                         // dense-cube stride of R
+    static constexpr int NCUBE = S * S * S;
+    static constexpr int o_R = o_E3k + NCD * NH2;           // [2][S^3] dense R cubes (+ 2 * (L+2) bases)
+    static constexpr int o_G = o_R + 2 * NCUBE + 2 * (L + 2);  // [2][NAB][NH2]; E3b [NAB][NH1] aliases it
     static constexpr int GSZ = 2 * NAB * NH2 > NAB * NH1 ? 2 * NAB * NH2 : NAB * NH1;
     static constexpr int o_YZ = o_G + GSZ;                  // y [NAB][NH1P] or z [NCD][NH2P]
     static constexpr int YZ = NAB * NH1P > NCD * NH2P ? NAB * NH1P : NCD * NH2P;
@@ -198,7 +200,7 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 const float th2 = (lane == 3) ? 1.0f : (ominf ? 1.0f : om2f / (om2f + rho));
                 float Fm[L + 2];
                 boys_mixed<L + 1>(T * th2, Fm, boys);
-                F *base = Rb + (lane == 3 ? 2 : 3) * NR;
+                F *base = Rb + 2 * Lay::NCUBE + (lane - 3) * (L + 2);
                 float f = pref * sqrtf(th2);
                 for (int n = 0; n <= L + 1; ++n) {
                     base[n] = (F)((n & 1) ? -f * Fm[n] : f * Fm[n]);
@@ -223,7 +225,7 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 const double th2 = (lane == 3) ? 1.0 : (ominf ? 1.0 : om2 / (om2 + rho));
                 double Fm[L + 2];
                 boys_fp64<L + 1>(T * th2, Fm, boys);
-                F *base = Rb + (lane == 3 ? 2 : 3) * NR;  // bases parked in the ping-pong slots
+                F *base = Rb + 2 * Lay::NCUBE + (lane - 3) * (L + 2);
                 if (FP32) {
                     // scaled basis: base'_n = pref theta (-theta^2)^n F_n, recursion with X s
                     double f = pref * sqrt(th2);
@@ -257,69 +259,46 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 }
             }
             group_sync(bar, GS);
-            // R tensors by levels: level n from level n+1 (ping-pong buffers)
+            // R tensors in two dense cubes R3[t][u][v] (stride S), level by
+            // level and, within a level, total by total from high to low, so
+            // each entry reads level n+1 values (as in hermite_R)
             {
+                constexpr int S = Lay::S, NCUBE = Lay::NCUBE;
                 const F X = scl[0], Y = scl[1], Z = scl[2];
                 const int nops = lr ? 2 : 1;
-                F *cur[2] = {Rb, Rb + NR}, *nxt[2] = {Rb + 2 * NR, Rb + 3 * NR};
-                // read the bases before the ping-pong slots are overwritten
-                F base0[L + 2], base1[L + 2];
-                for (int n = 0; n <= L + 1; ++n) {
-                    base0[n] = Rb[2 * NR + n];
-                    base1[n] = lr ? Rb[3 * NR + n] : F(0);
-                }
-                group_sync(bar, GS);
-                if (lane == 0) {
-                    cur[0][0] = base0[L + 1];
-                    if (lr) cur[1][0] = base1[L + 1];
-                }
+                const F *bases = Rb + 2 * NCUBE;
+                if (lane < nops) Rb[lane * NCUBE] = bases[lane * (L + 2) + L + 1];
                 group_sync(bar, GS);
                 for (int n = L; n >= 0; --n) {
-                    const int K = L + 1 - n;  // totals 0..K at level n
-                    const int cnt = nherm(K);
-                    for (int it = lane; it < nops * cnt; it += GS) {
-                        const int o = it / cnt, h = it % cnt;
-                        const F *src = cur[o];
-                        F r;
-                        if (h == 0) {
-                            r = o == 0 ? base0[n] : base1[n];
-                        } else {
-                            int k = 0;
-                            while (nherm(k) <= h) ++k;
-                            const int rr = h - nherm(k - 1);
+                    for (int k = L + 1 - n; k >= 1; --k) {
+                        const int cnt = (k + 1) * (k + 2) / 2;  // triples of total k
+                        for (int it = lane; it < nops * cnt; it += GS) {
+                            const int o = it / cnt, r = it % cnt;
                             int s = 0;
-                            while ((s + 1) * (s + 2) / 2 <= rr) ++s;
-                            const int v = rr - s * (s + 1) / 2, u = s - v, t = k - s;
+                            while ((s + 1) * (s + 2) / 2 <= r) ++s;
+                            const int v = r - s * (s + 1) / 2, u = s - v, t = k - s;
+                            F *c = Rb + o * NCUBE;
+                            F val;
                             if (t > 0) {
-                                r = X * src[hidx(t - 1, u, v)];
-                                if (t > 1) r += F(t - 1) * src[hidx(t - 2, u, v)];
+                                val = X * c[((t - 1) * S + u) * S + v];
+                                if (t > 1) val += F(t - 1) * c[((t - 2) * S + u) * S + v];
                             } else if (u > 0) {
-                                r = Y * src[hidx(t, u - 1, v)];
-                                if (u > 1) r += F(u - 1) * src[hidx(t, u - 2, v)];
+                                val = Y * c[(t * S + u - 1) * S + v];
+                                if (u > 1) val += F(u - 1) * c[(t * S + u - 2) * S + v];
                             } else {
-                                r = Z * src[hidx(t, u, v - 1)];
-                                if (v > 1) r += F(v - 1) * src[hidx(t, u, v - 2)];
+                                val = Z * c[(t * S + u) * S + v - 1];
+                                if (v > 1) val += F(v - 1) * c[(t * S + u) * S + v - 2];
                             }
+                            c[(t * S + u) * S + v] = val;
                         }
-                        nxt[o][h] = r;
+                        group_sync(bar, GS);
                     }
-                    group_sync(bar, GS);
-                    F *tmp0 = cur[0], *tmp1 = cur[1];
-                    cur[0] = nxt[0];
-                    cur[1] = nxt[1];
-                    nxt[0] = tmp0;
-                    nxt[1] = tmp1;
-                }
-                // after an even number of swaps R sits in the first slots; copy if not
-                if (cur[0] != Rb) {
-                    for (int it = lane; it < nops * NR; it += GS) {
-                        const int o = it / NR, h = it % NR;
-                        Rb[o * NR + h] = cur[o][h];
-                    }
+                    if (lane < nops) Rb[lane * NCUBE] = bases[lane * (L + 2) + n];
                     group_sync(bar, GS);
                 }
             }
-            const F *R = Rb, *Rl = Rb + NR;
+            constexpr int S = Lay::S;
+            const F *R3 = Rb, *R3l = Rb + Lay::NCUBE;
             const F *spow = scl + 16;
             // ket products E3k[cd][h2] (times s^{|h2|} in fp32)
             for (int it = lane; it < NCD * NH2; it += GS) {
@@ -370,7 +349,9 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 G[NAB * NH2 + it] = s1;
             }
             group_sync(bar, GS);
-            // y[ab][h1] = sum_h2 G[ab][h2] R[h1+h2] (+ lr), times s^{|h1|}
+            // y[ab][h1] = sum_h2 G[ab][h2] R[h1+h2] (+ lr), times s^{|h1|}; the
+            // cube index of h1+h2 is base(h1) + off(h2) with off a constant of
+            // the unrolled h2 loop
             for (int it = lane; it < NAB * NH1P; it += GS) {
                 const int ab = it / NH1P, h1 = it % NH1P;
                 int n1 = 0;
@@ -379,16 +360,20 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 int s1 = 0;
                 while ((s1 + 1) * (s1 + 2) / 2 <= r1) ++s1;
                 const int v1 = r1 - s1 * (s1 + 1) / 2, u1 = s1 - v1, t1 = n1 - s1;
-                F y = F(0);
+                const int b1 = (t1 * S + u1) * S + v1;
                 const F *g0 = G + ab * NH2, *g1 = G + NAB * NH2 + ab * NH2;
-                int h2 = 0;
+                F y0 = F(0), y1 = F(0);
+#pragma unroll
                 for (int t2 = 0; t2 <= L2; ++t2)
+#pragma unroll
                     for (int u2 = 0; u2 <= L2 - t2; ++u2)
-                        for (int v2 = 0; v2 <= L2 - t2 - u2; ++v2, ++h2) {
-                            const int hr = hidx(t1 + t2, u1 + u2, v1 + v2);
-                            y += g0[hidx(t2, u2, v2)] * R[hr];
-                            if (lr) y += g1[hidx(t2, u2, v2)] * Rl[hr];
+#pragma unroll
+                        for (int v2 = 0; v2 <= L2 - t2 - u2; ++v2) {
+                            const int off = (t2 * S + u2) * S + v2;
+                            y0 += g0[hidx(t2, u2, v2)] * R3[b1 + off];
+                            if (lr) y1 += g1[hidx(t2, u2, v2)] * R3l[b1 + off];
                         }
+                F y = y0 + y1;
                 if constexpr (FP32) y *= spow[n1];
                 YZ[it] = y;
             }
@@ -454,21 +439,26 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 int s2 = 0;
                 while ((s2 + 1) * (s2 + 2) / 2 <= r2) ++s2;
                 const int v2 = r2 - s2 * (s2 + 1) / 2, u2 = s2 - v2, t2 = n2 - s2;
-                F z = F(0);
+                const int b2 = (t2 * S + u2) * S + v2;
                 const F *f0 = Fr + cd * NH1, *f1 = Fr + NCD * NH1 + cd * NH1;
+                F z0 = F(0), z1 = F(0);
+#pragma unroll
                 for (int t1 = 0; t1 <= L1; ++t1)
+#pragma unroll
                     for (int u1 = 0; u1 <= L1 - t1; ++u1)
+#pragma unroll
                         for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
-                            const int h1 = hidx(t1, u1, v1), hr = hidx(t1 + t2, u1 + u2, v1 + v2);
+                            const int off = (t1 * S + u1) * S + v1;
                             if constexpr (FP32) {
                                 const F sh = spow[t1 + u1 + v1];
-                                z += f0[h1] * sh * R[hr];
-                                if (lr) z += f1[h1] * sh * Rl[hr];
+                                z0 += f0[hidx(t1, u1, v1)] * sh * R3[b2 + off];
+                                if (lr) z1 += f1[hidx(t1, u1, v1)] * sh * R3l[b2 + off];
                             } else {
-                                z += f0[h1] * R[hr];
-                                if (lr) z += f1[h1] * Rl[hr];
+                                z0 += f0[hidx(t1, u1, v1)] * R3[b2 + off];
+                                if (lr) z1 += f1[hidx(t1, u1, v1)] * R3l[b2 + off];
                             }
                         }
+                F z = z0 + z1;
                 if constexpr (FP32) z *= spow[n2];
                 YZ[it] = (n2 & 1) ? -z : z;
             }
@@ -668,37 +658,52 @@ struct CoopChoice {
 
 namespace tg {
 
+// fp64: the cooperative kernel (shared memory, DFMA bound) for every class
+// with at least 54 function quartets; fp32: the register-resident thread
+// kernel, except for the two largest classes.
 template <int LA, int LB, int LC, int LD>
 struct UseCoop {
-    // measured on the 32-atom workload: the cooperative form wins only for the
-    // two largest classes, (dd|dp) and (dd|dd)
-    static constexpr bool value = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD) >= 648;
+    static constexpr int nfq = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
+    static constexpr bool fp64 = nfq >= 54;
+    static constexpr bool fp32 = nfq >= 648;
 };
+
+template <int LA, int LB, int LC, int LD, typename F>
+cudaError_t launch_coop(int grid, size_t smem, cudaStream_t st, const MolDesc *mols, const ClassLaunch &cl,
+                        const OutArgs &out, const double *boys)
+{
+    using C = CoopChoice<LA, LB, LC, LD, F>;
+    auto kern = k_grad_coop<LA, LB, LC, LD, F, C::GS>;
+    const size_t sm = smem + C::bytes_all();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
+    return cudaGetLastError();
+}
 
 template <int LA, int LB, int LC, int LD>
 cudaError_t launch_class_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const MolDesc *mols,
                                 const ClassLaunch &cl, const OutArgs &out, const double *boys)
 {
-    if constexpr (UseCoop<LA, LB, LC, LD>::value) {
-        cudaError_t e;
-        if (fp32) {
-            using C = CoopChoice<LA, LB, LC, LD, float>;
-            auto kern = k_grad_coop<LA, LB, LC, LD, float, C::GS>;
-            const size_t sm = smem + C::bytes_all();
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    using U = UseCoop<LA, LB, LC, LD>;
+    if (fp32) {
+        if constexpr (U::fp32) return launch_coop<LA, LB, LC, LD, float>(grid, smem, st, mols, cl, out, boys);
+        else {
+            auto kern = k_grad<LA, LB, LC, LD, true>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
-        } else {
-            using C = CoopChoice<LA, LB, LC, LD, double>;
-            auto kern = k_grad_coop<LA, LB, LC, LD, double, C::GS>;
-            const size_t sm = smem + C::bytes_all();
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
+            kern<<<grid, TILE, smem, st>>>(mols, cl, out, boys);
+            return cudaGetLastError();
         }
-        return cudaGetLastError();
     } else {
-        return launch_thread_kernel<LA, LB, LC, LD>(fp32, grid, smem, st, mols, cl, out, boys);
+        if constexpr (U::fp64) return launch_coop<LA, LB, LC, LD, double>(grid, smem, st, mols, cl, out, boys);
+        else {
+            auto kern = k_grad<LA, LB, LC, LD, false>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            kern<<<grid, TILE, smem, st>>>(mols, cl, out, boys);
+            return cudaGetLastError();
+        }
     }
 }
 

@@ -74,6 +74,17 @@ def test_c2_full_size_shards(tg):
         assert np.abs(g - ref).max() <= TOL
 
 
+def test_c4_full_size_shard(tg):
+    """The 300-atom core + water cluster (2790 basis functions) at full size:
+    every tile of every class is launched, the shard filter keeps 1/50000 of
+    the canonical quartets, and the oracle evaluates the same shard."""
+    s = synth.config(3)
+    g, st = tg.grad2e(s, screen_tol=1e-10, rank=11, nranks=50000)
+    ref, _, nq = oracle.grad2e(s, tau=1e-10, rank=11, nranks=50000)
+    assert st["quartets"] == nq and nq > 1000
+    assert np.abs(g - ref).max() <= TOL
+
+
 def test_bitwise_deterministic(tg, c1):
     g1, _ = tg.grad2e(c1, screen_tol=1e-12)
     g2, _ = tg.grad2e(c1, screen_tol=1e-12)
