@@ -318,7 +318,7 @@ def main():
         pk = peaks["fp32" if fp32 else "fp64"]
         nc = lambda l: (l + 1) * (l + 2) // 2
         nfq = nc(la) * nc(lb) * nc(lc) * nc(ld)
-        coop = nfq >= (648 if fp32 else 54)  # the library's kernel choice per class
+        coop = nfq >= (648 if fp32 else 216)  # the library's default kernel per class
         kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if coop else "",
                                                names[la], names[lb], names[lc], names[ld],
                                                "fp32" if fp32 else "fp64")

@@ -92,7 +92,10 @@ typedef struct {
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
     int rank, nranks;       /* shard; default 0 / 1 */
     int timing;             /* 1: time every class kernel with CUDA events (tg_stats.class_ms) */
-    int reserved[7];
+    int reserved[7];        /* [0]: tg_batch_create autotuning (below); [1]: class kernel kind,
+                               0 = per-class default, 1 = one quartet per thread, 2 = a thread
+                               group per quartet where compiled (same results to rounding);
+                               others 0 */
 } tg_options;
 
 typedef struct {
@@ -140,8 +143,9 @@ const char *tg_strerror(int status);
  * (a basis holds one plan at a time) and must outlive the batch; with
  * device_ptrs the densities are read from the caller's device buffers at
  * every run (their contents may change, the plan does not), otherwise they
- * are copied at creation.  opt->reserved[0] = 1 autotunes the persistent
- * grid (1-4 CTAs per SM) of every class list on a sample of its tiles.
+ * are copied at creation.  opt->reserved[0] = 1 autotunes every class list
+ * on a sample of its tiles: the kernel kind (one quartet per thread, or a
+ * group of threads per quartet) and the persistent grid (1-4 CTAs per SM).
  * tg_batch_run replays the graph on opt->stream and writes grads[m]
  * (natom_m * 3, host unless device_ptrs).  Not part of the paper, which
  * evaluates one system at a time (Sec. II.C). */

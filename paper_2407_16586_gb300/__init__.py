@@ -228,10 +228,13 @@ class Basis:
         return X[:n.value].copy(), y[:n.value].copy(), e[:n.value].copy()
 
     def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
-               timing=False, router=None, mixed_tol=1e-6):
+               timing=False, router=None, mixed_tol=1e-6, kernel=0):
         """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
-        torch CUDA tensors (then the densities and ``out`` stay on the device)."""
+        torch CUDA tensors (then the densities and ``out`` stay on the device).  ``kernel``
+        picks the class kernels: 0 per-class default, 1 one quartet per thread, 2 a thread
+        group per quartet where compiled."""
         opt = tg_options_default()
+        opt.reserved[1] = int(kernel)
         opt.screen_tol = float(screen_tol)
         opt.precision = int(precision)
         opt.rank, opt.nranks = int(rank), int(nranks)

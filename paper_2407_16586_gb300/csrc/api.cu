@@ -466,7 +466,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
         for (auto &hp : pl.cls[c]) npp_max += hp.np;
     }
     // ---- arena 2: pair arrays, primitive-pair records, tiles, features, partials
-    pl.G = std::max(1, 2 * b->nsm);
+    pl.G = std::max(1, 4 * b->nsm);  // partial slabs: up to 4 resident CTAs per SM
     {
         const size_t np_k = (size_t)std::max<long long>(nk_all, 1);
         const size_t npp = (size_t)std::max<long long>(npp_max, 1);
@@ -796,7 +796,7 @@ void build_exec(const std::vector<const Plan *> &plans, const std::vector<std::v
 // components go to dump[(list position * TILE + thread) * 12 + c].
 int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, double *d_part,
                 unsigned long long *dcnt, double *dump, const double *boys, int G, const int *grids, bool timing,
-                cudaStream_t st, tg_stats *stats, int &launches)
+                cudaStream_t st, tg_stats *stats, int &launches, const int *kinds = nullptr, int kind_all = 0)
 {
     OutArgs out;
     out.partials = d_part;
@@ -831,11 +831,12 @@ int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, dou
             cl.Q = Qc;
             cl.ntiles = nt;
             cl.tiles = d_tiles + ex.off[k];
+            cl.nsplit = cl.nchunk = 1;
+            cl.kind = kinds ? kinds[k] : kind_all;
             OutArgs o = out;
             o.counters = dcnt + 4 * qc;
             if (dump) o.dump = dump + (size_t)ex.off[k] * TILE * 12;
-            const int g0 = (grids && grids[k] > 0) ? grids[k] : G;
-            const int grid = (int)std::min<long long>(nt, g0);
+            const int grid = std::min(G, (grids && grids[k] > 0) ? grids[k] : G);  // cap; the launcher sizes it
             if (timing) cudaEventRecord(e0, st);
             cudaError_t e = kClassLaunchers[qc](r, grid, smem, st, d_mols, cl, o, boys);
             if (e != cudaSuccess) {
@@ -896,7 +897,7 @@ struct tg_batch {
     uint4 *d_tiles = nullptr;
     double *d_part = nullptr, *d_grad = nullptr;
     unsigned long long *d_cnt = nullptr;
-    std::vector<int> grids;
+    std::vector<int> grids, kinds;
     int G = 1;
     int device_ptrs = 0;
     cudaStream_t cap = nullptr;
@@ -948,7 +949,7 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
     if (stats)
         for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
     rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, nullptr, b->d_boys, pl.G, nullptr, opt.timing != 0, st,
-                     stats, launches);
+                     stats, launches, nullptr, opt.reserved[1]);
     if (rc != TG_OK) return rc;
     k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, pl.G, d_part, pl.dgrad);
     ++launches;
@@ -1140,10 +1141,12 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
                            cudaMemcpyHostToDevice));
     const double *boys = bt->bases[0]->d_boys;
 
-    // ---- autotune the persistent grid of every (class, precision) list on a
-    // sample of its tiles: 1, 2, 3 or 4 CTAs per SM, fastest kept
+    // ---- autotune every (class, precision) list on a sample of its tiles:
+    // thread or cooperative kernel, grid capped at 1, 2, 3 or 4 CTAs per SM;
+    // the fastest pair is kept
     bt->grids.assign(2 * NQC, G);
-    const int nsm = std::max(1, G / 2);
+    bt->kinds.assign(2 * NQC, opt.reserved[1]);
+    const int nsm = std::max(1, bt->bases[0]->nsm);
     if (opt.reserved[0] == 1) {
         cudaEvent_t e0, e1;
         TG_CUDA(cudaEventCreate(&e0));
@@ -1156,27 +1159,29 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
             sub.natom_max = natom_max;
             const long long ns = std::min<long long>(nt, 8LL * nsm);
             for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : ns;
-            float best = 0.f;
-            for (int mult = 1; mult <= 4; ++mult) {
-                std::vector<int> gr(2 * NQC, mult * nsm);
-                int dummy = 0;
-                cudaEventRecord(e0, st);
-                int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt, nullptr,
-                                     boys, G, gr.data(), false, st, nullptr, dummy);
-                cudaEventRecord(e1, st);
-                if (rc != TG_OK) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return rc;
+            float best = -1.f;
+            for (int kind = 1; kind <= 2; ++kind)
+                for (int mult = 1; mult <= 4; ++mult) {
+                    std::vector<int> gr(2 * NQC, mult * nsm), kd(2 * NQC, kind);
+                    int dummy = 0;
+                    cudaEventRecord(e0, st);
+                    int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt,
+                                         nullptr, boys, G, gr.data(), false, st, nullptr, dummy, kd.data());
+                    cudaEventRecord(e1, st);
+                    if (rc != TG_OK) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return rc;
+                    }
+                    TG_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (best < 0.f || ms < best) {
+                        best = ms;
+                        bt->grids[k] = mult * nsm;
+                        bt->kinds[k] = kind;
+                    }
                 }
-                TG_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (mult == 1 || ms < best) {
-                    best = ms;
-                    bt->grids[k] = mult * nsm;
-                }
-            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1210,7 +1215,7 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
         cudaMemsetAsync(bt->d_part, 0, sizeof(double) * (size_t)G * 3 * natom_total, bt->cap);
         cudaMemsetAsync(bt->d_cnt, 0, sizeof(unsigned long long) * 4 * NQC, bt->cap);
         int rc = launch_exec(bt->ex, bt->d_mols, bt->d_tiles, bt->d_part, bt->d_cnt, nullptr, boys, G,
-                             bt->grids.data(), false, bt->cap, nullptr, n);
+                             bt->grids.data(), false, bt->cap, nullptr, n, bt->kinds.data());
         k_reduce<<<(3 * natom_total + 127) / 128, 128, 0, bt->cap>>>(3 * natom_total, G, bt->d_part, bt->d_grad);
         ++n;
         if (pass == 1) {

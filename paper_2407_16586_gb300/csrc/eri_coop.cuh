@@ -57,8 +57,8 @@ __device__ __forceinline__ int ebi(int i, int j, int t, int J1, int T1) { return
 // reduces them over the group.
 template <int LA, int LB, int LC, int LD, typename F, int GS>
 __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp,
-                             int sa, int sb, int sc, int sd, int pb0, int nbp, int pk0, int nkp, double scale,
-                             const double *boys, double (&acc)[9])
+                             int sa, int sb, int sc, int sd, int pb0, int nbp, int ib0, int ibs, int pk0, int nkp,
+                             double scale, const double *boys, double (&acc)[9])
 {
     using Lay = CoopLayout<LA, LB, LC, LD, F>;
     constexpr int NB = Lay::NB, ND = Lay::ND, NAB = Lay::NAB, NCD = Lay::NCD;
@@ -102,7 +102,7 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
     }
     group_sync(bar, GS);
 
-    for (int ib = 0; ib < nbp; ++ib) {
+    for (int ib = ib0; ib < nbp; ib += ibs) {
         const int ip = pb0 + ib;
         const double p = pp.p[ip], Px = pp.Px[ip], Py = pp.Py[ip], Pz = pp.Pz[ip];
         // 1-D bra Hermite tables, one direction per lane
@@ -532,8 +532,13 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
     double *slab = out.partials + (size_t)blockIdx.x * out.natom_total * 3;
     int cur = -1, cur_off3 = 0, cur_n3 = 0;
     unsigned long long nq = 0, npq = 0;
-    for (long long it = blockIdx.x; it < cl.ntiles; it += gridDim.x) {
-        const uint4 tl = cl.tiles[it];
+    // unit = (tile, chunk, split): chunk c holds quartets c * QPC ... of the
+    // tile, split s takes the bra primitive pairs s, s + S, ...
+    const int S = cl.nsplit, C = cl.nchunk, QPC = TILE / C;
+    for (long long it = blockIdx.x; it < cl.ntiles * C * S; it += gridDim.x) {
+        const long long tile = it / (C * S);
+        const int chunk = (int)((it / S) % C), split = (int)(it % S);
+        const uint4 tl = cl.tiles[tile];
         const int mol = (int)tl.x;
         if (mol != cur) {
             if (out.use_smem) {
@@ -553,7 +558,12 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
         const PrimPairs pp = md.pp;
         const ScreenArgs scr = md.scr;
         const bool same = cl.P == cl.Q;
-        for (int qi = grp; qi < TILE; qi += NG) {
+        if (C > 1 && !out.dump) {
+            for (int k = threadIdx.x; k < TILE * 12; k += blockDim.x) stg[k] = 0.0;
+            for (int k = threadIdx.x; k < TILE * 4; k += blockDim.x) sat[k] = -1;
+            __syncthreads();
+        }
+        for (int qi = chunk * QPC + grp; qi < (chunk + 1) * QPC; qi += NG) {
             const int bi = tl.y * TB + qi / TK;
             const int ki = tl.z * TK + qi % TK;
             double g[12];
@@ -561,6 +571,7 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
             for (int k = 0; k < 12; ++k) g[k] = 0.0;
             int at[4] = {-1, -1, -1, -1};
             bool ok = bi < bra.n && ki < ket.n && (!same || bi >= ki);
+            if (ok) ok = split < bra.np[bi];
             int sa = 0, sb = 0, sc = 0, sd = 0;
             if (ok) {
                 sa = bra.sa[bi];
@@ -579,7 +590,7 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
 #pragma unroll
                 for (int k = 0; k < 9; ++k) acc[k] = 0.0;
                 quartet_coop<LA, LB, LC, LD, F, GS>(gsm, lane, bar, geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi],
-                                                    nbp, ket.poff[ki], nkp, scale, boys, acc);
+                                                    nbp, split, S, ket.poff[ki], nkp, scale, boys, acc);
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
 #pragma unroll
@@ -608,14 +619,14 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
                     at[1] = geo.sh_atom[sb];
                     at[2] = geo.sh_atom[sc];
                     at[3] = geo.sh_atom[sd];
-                    nq += 1;
-                    npq += (unsigned long long)nbp * nkp;
+                    if (split == 0) nq += 1;
+                    npq += (unsigned long long)((nbp - split + S - 1) / S) * nkp;
                 }
                 group_sync(bar, GS);
             }
             if (lane == 0) {
                 if (out.dump) {
-                    double *d = out.dump + ((size_t)it * TILE + qi) * 12;
+                    double *d = out.dump + ((size_t)tile * TILE + qi) * 12;  // one unit per tile
 #pragma unroll
                     for (int k = 0; k < 12; ++k) d[k] = g[k];
                 } else {
@@ -637,7 +648,7 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
         nq += __shfl_xor_sync(0xffffffffu, nq, o);
         npq += __shfl_xor_sync(0xffffffffu, npq, o);
     }
-    if ((threadIdx.x & 31) == 0 && nq) {
+    if ((threadIdx.x & 31) == 0 && (nq || npq)) {  // a split unit may hold primitives only
         atomicAdd(out.counters + 0, nq);
         atomicAdd(out.counters + (sizeof(F) == 4 ? 3 : 1), npq);
         if (sizeof(F) == 4) atomicAdd(out.counters + 2, nq);
@@ -658,53 +669,50 @@ struct CoopChoice {
 
 namespace tg {
 
-// fp64: the cooperative kernel (shared memory, DFMA bound) for every class
-// with at least 54 function quartets; fp32: the register-resident thread
-// kernel, except for the two largest classes.
+// Kernel kind per class: the cooperative kernel is compiled for the fp64
+// classes with at least 54 function quartets and the fp32 classes with at
+// least 648, the thread kernel for every class below 648 (above, its
+// per-thread arrays run to tens of KB of local memory).  By default the
+// cooperative kernel runs for the fp64 classes from 216 function quartets
+// on ((dd|ds) and larger, measured faster there) and wherever it is the
+// only one.  ClassLaunch::kind = 1 / 2 forces the
+// thread / cooperative kernel where both exist.
 template <int LA, int LB, int LC, int LD>
 struct UseCoop {
     static constexpr int nfq = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
     static constexpr bool fp64 = nfq >= 54;
     static constexpr bool fp32 = nfq >= 648;
+    static constexpr bool thread = nfq < 648;
+    static constexpr bool fp64_default = nfq >= 216;
 };
 
 template <int LA, int LB, int LC, int LD, typename F>
-cudaError_t launch_coop(int grid, size_t smem, cudaStream_t st, const MolDesc *mols, const ClassLaunch &cl,
+cudaError_t launch_coop(int gcap, size_t smem, cudaStream_t st, const MolDesc *mols, const ClassLaunch &cl,
                         const OutArgs &out, const double *boys)
 {
     using C = CoopChoice<LA, LB, LC, LD, F>;
-    auto kern = k_grad_coop<LA, LB, LC, LD, F, C::GS>;
-    const size_t sm = smem + C::bytes_all();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
-    return cudaGetLastError();
+    return launch_units(k_grad_coop<LA, LB, LC, LD, F, C::GS>, TILE / C::GS, gcap, smem + C::bytes_all(), st, mols,
+                        cl, out, boys);
 }
 
 template <int LA, int LB, int LC, int LD>
-cudaError_t launch_class_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const MolDesc *mols,
+cudaError_t launch_class_kernel(int fp32, int gcap, size_t smem, cudaStream_t st, const MolDesc *mols,
                                 const ClassLaunch &cl, const OutArgs &out, const double *boys)
 {
     using U = UseCoop<LA, LB, LC, LD>;
     if (fp32) {
-        if constexpr (U::fp32) return launch_coop<LA, LB, LC, LD, float>(grid, smem, st, mols, cl, out, boys);
-        else {
-            auto kern = k_grad<LA, LB, LC, LD, true>;
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            kern<<<grid, TILE, smem, st>>>(mols, cl, out, boys);
-            return cudaGetLastError();
+        if constexpr (U::fp32) {
+            if (!U::thread || cl.kind != 1)
+                return launch_coop<LA, LB, LC, LD, float>(gcap, smem, st, mols, cl, out, boys);
         }
     } else {
-        if constexpr (U::fp64) return launch_coop<LA, LB, LC, LD, double>(grid, smem, st, mols, cl, out, boys);
-        else {
-            auto kern = k_grad<LA, LB, LC, LD, false>;
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            kern<<<grid, TILE, smem, st>>>(mols, cl, out, boys);
-            return cudaGetLastError();
+        if constexpr (U::fp64) {
+            if (!U::thread || cl.kind == 2 || (cl.kind == 0 && U::fp64_default))
+                return launch_coop<LA, LB, LC, LD, double>(gcap, smem, st, mols, cl, out, boys);
         }
     }
+    if constexpr (U::thread) return launch_thread_kernel<LA, LB, LC, LD>(fp32, gcap, smem, st, mols, cl, out, boys);
+    return cudaErrorInvalidValue;  // not reached: classes without a thread kernel return above
 }
 
 }  // namespace tg

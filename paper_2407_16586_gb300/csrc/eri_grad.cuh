@@ -101,8 +101,8 @@ __device__ __forceinline__ void build_gamma(const DensArgs &den, int fa, int fb,
 // (x, y, z each) of sum Gamma (ab|cd) over both operators.
 template <int LA, int LB, int LC, int LD>
 __device__ void quartet_fp64(const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp, int sa, int sb, int sc,
-                             int sd, int pb0, int nbp, int pk0, int nkp, double scale, const double *boys,
-                             double (&g)[12])
+                             int sd, int pb0, int nbp, int ib0, int ibs, int pk0, int nkp, double scale,
+                             const double *boys, double (&g)[12])
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int NAB = NA * NB, NCD = NC * ND;
@@ -125,7 +125,7 @@ __device__ void quartet_fp64(const GeoArgs &geo, const DensArgs &den, const Prim
 
     double gA[3] = {0, 0, 0}, gC[3] = {0, 0, 0}, gT[3] = {0, 0, 0};
 
-    for (int ib = 0; ib < nbp; ++ib) {
+    for (int ib = ib0; ib < nbp; ib += ibs) {
         const int ip = pb0 + ib;
         const double p = pp.p[ip], Px = pp.Px[ip], Py = pp.Py[ip], Pz = pp.Pz[ip], Kab = pp.K[ip];
         const double za2 = 2.0 * pp.za[ip];
@@ -436,331 +436,10 @@ __device__ __forceinline__ void boys_mixed(float T, float (&F)[M + 1], const dou
 // One canonical shell quartet with fp32 primitive arithmetic.  Same algebra
 // as quartet_fp64, in the scaled Hermite basis R'_h = R_h / s^{|h|},
 // s = sqrt(2 rho): R'^{(n)}_{000} = pref (-1)^n F_n and the recursion runs
-// with X s, so every intermediate stays within fp32 range for any exponent.
-// The factors s^{|h|} are moved onto the short Hermite vectors (G rows,
-// F rows, y, z).  Each bra primitive's contribution is added in fp64.
-template <int LA, int LB, int LC, int LD>
-__device__ void quartet_fp32(const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp, int sa, int sb, int sc,
-                             int sd, int pb0, int nbp, int pk0, int nkp, double scale, const double *boys,
-                             double (&g)[12])
-{
-    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
-    constexpr int NAB = NA * NB, NCD = NC * ND;
-    constexpr int L1 = LA + LB, L2 = LC + LD, L = L1 + L2;
-    constexpr int NH1 = nherm(L1), NH1P = nherm(L1 + 1), NH2 = nherm(L2), NH2P = nherm(L2 + 1);
-    constexpr int NR = nherm(L + 1);
-    constexpr bool UAB = NAB * NH1P * NH2 <= 64;
-    constexpr bool UCD = NCD * NH2P * NH1 <= 64;
-
-    float gam[NAB * NCD], gaml[NAB * NCD];
-    {
-        double gd[NAB * NCD], gdl[NAB * NCD];
-        build_gamma<LA, LB, LC, LD>(den, geo.sh_bf[sa], geo.sh_bf[sb], geo.sh_bf[sc], geo.sh_bf[sd], scale, gd, gdl);
-        for (int k = 0; k < NAB * NCD; ++k) {
-            gam[k] = (float)gd[k];
-            gaml[k] = (float)gdl[k];
-        }
-    }
-    const bool lr = den.use_lr;
-    const double om2 = den.omega * den.omega;
-    const bool ominf = isinf(den.omega);
-
-    const double *xa = geo.xyz + 3 * geo.sh_atom[sa], *xc = geo.xyz + 3 * geo.sh_atom[sc];
-    const float ACx = (float)(xa[0] - xc[0]), ACy = (float)(xa[1] - xc[1]), ACz = (float)(xa[2] - xc[2]);
-    const float om2f = (float)om2;
-
-    double gA[3] = {0, 0, 0}, gC[3] = {0, 0, 0}, gT[3] = {0, 0, 0};
-
-    for (int ib = 0; ib < nbp; ++ib) {
-        const int ip = pb0 + ib;
-        const long long nr = pp.n;
-        const float pf = pp.fp[ip], Kab = pp.fK[ip];
-        const float PAx = pp.fPA[ip], PAy = pp.fPA[nr + ip], PAz = pp.fPA[2 * nr + ip];
-        const float za2 = 2.0f * pp.fza[ip];
-        const float oo2p = 0.5f / pf;
-        float Ebx[LA + 2][LB + 1][L1 + 2], Eby[LA + 2][LB + 1][L1 + 2], Ebz[LA + 2][LB + 1][L1 + 2];
-        etab<LA + 1, LB>(Ebx, PAx, pp.fPB[ip], oo2p);
-        etab<LA + 1, LB>(Eby, PAy, pp.fPB[nr + ip], oo2p);
-        etab<LA + 1, LB>(Ebz, PAz, pp.fPB[2 * nr + ip], oo2p);
-
-        float Fa[NCD][NH1], Fl[NCD][NH1];
-#pragma unroll
-        for (int k = 0; k < NCD; ++k)
-#pragma unroll
-            for (int h = 0; h < NH1; ++h) {
-                Fa[k][h] = 0.0f;
-                Fl[k][h] = 0.0f;
-            }
-        {
-            int ab = 0;
-            for_pairs<LA, LB, UAB>([&](int ax, int ay, int az, int bx, int by, int bz) {
-                for (int t = 0; t <= ax + bx; ++t)
-                    for (int u = 0; u <= ay + by; ++u)
-                        for (int v = 0; v <= az + bz; ++v) {
-                            const float e = Ebx[ax][bx][t] * Eby[ay][by][u] * Ebz[az][bz][v];
-                            const int h = hidx(t, u, v);
-#pragma unroll
-                            for (int k = 0; k < NCD; ++k) {
-                                Fa[k][h] += gam[ab * NCD + k] * e;
-                                if (lr) Fl[k][h] += gaml[ab * NCD + k] * e;
-                            }
-                        }
-                ++ab;
-            });
-        }
-
-        float fA[3] = {0.f, 0.f, 0.f}, fC[3] = {0.f, 0.f, 0.f}, fT[3] = {0.f, 0.f, 0.f};
-        for (int jk = 0; jk < nkp; ++jk) {
-            const int kp = pk0 + jk;
-            const float qf = pp.fp[kp], Kcd = pp.fK[kp];
-            const float QCx = pp.fPA[kp], QCy = pp.fPA[nr + kp], QCz = pp.fPA[2 * nr + kp];
-            const float zc2 = 2.0f * pp.fza[kp];
-            const float oo2q = 0.5f / qf;
-            float Ekx[LC + 2][LD + 1][L2 + 2], Eky[LC + 2][LD + 1][L2 + 2], Ekz[LC + 2][LD + 1][L2 + 2];
-            etab<LC + 1, LD>(Ekx, QCx, pp.fPB[kp], oo2q);
-            etab<LC + 1, LD>(Eky, QCy, pp.fPB[nr + kp], oo2q);
-            etab<LC + 1, LD>(Ekz, QCz, pp.fPB[2 * nr + kp], oo2q);
-
-            // P - Q = (P - A) - (Q - C) + (A - C), all terms small
-            const float pq = pf + qf;
-            const float rho = pf * qf / pq;
-            const float Xd = PAx - QCx + ACx, Yd = PAy - QCy + ACy, Zd = PAz - QCz + ACz;
-            const float T = rho * (Xd * Xd + Yd * Yd + Zd * Zd);
-            const float sc_ = sqrtf(2.0f * rho);
-            const float pref = 34.986836655249725f * rsqrtf(pq) / (pf * qf) * Kab * Kcd;
-            float spow[L + 3];
-            spow[0] = 1.0f;
-#pragma unroll
-            for (int n = 1; n <= L + 2; ++n) spow[n] = spow[n - 1] * sc_;
-            float R[NR], Rl[NR];
-            {
-                float Fm[L + 2], base[L + 2];
-                boys_mixed<L + 1>(T, Fm, boys);
-#pragma unroll
-                for (int n = 0; n <= L + 1; ++n) base[n] = (n & 1) ? -pref * Fm[n] : pref * Fm[n];
-                hermite_R<L + 1>(R, base, (float)Xd * sc_, (float)Yd * sc_, (float)Zd * sc_);
-                if (lr) {
-                    const float th2 = ominf ? 1.0f : om2f / (om2f + rho);
-                    boys_mixed<L + 1>(T * th2, Fm, boys);
-                    float f = pref * sqrtf(th2);
-                    const float t2 = th2;
-#pragma unroll
-                    for (int n = 0; n <= L + 1; ++n) {
-                        base[n] = (n & 1) ? -f * Fm[n] : f * Fm[n];
-                        f *= t2;
-                    }
-                    hermite_R<L + 1>(Rl, base, (float)Xd * sc_, (float)Yd * sc_, (float)Zd * sc_);
-                }
-            }
-
-            float E3k[NCD][NH2];
-            {
-                int cd = 0;
-                for_pairs<LC, LD, true>([&](int cx, int cy, int cz, int dx, int dy, int dz) {
-#pragma unroll
-                    for (int h = 0; h < NH2; ++h) E3k[cd][h] = 0.0f;
-#pragma unroll
-                    for (int t = 0; t <= cx + dx; ++t)
-#pragma unroll
-                        for (int u = 0; u <= cy + dy; ++u)
-#pragma unroll
-                            for (int v = 0; v <= cz + dz; ++v)
-                                E3k[cd][hidx(t, u, v)] =
-                                    Ekx[cx][dx][t] * Eky[cy][dy][u] * Ekz[cz][dz][v] * spow[t + u + v];
-                    ++cd;
-                });
-            }
-
-            {
-                int ab = 0;
-                for_pairs<LA, LB, UAB>([&](int ax, int ay, int az, int bx, int by, int bz) {
-                    float gr[NH2], grl[NH2];
-#pragma unroll 1
-                    for (int h = 0; h < NH2; ++h) {
-                        float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-                        for (int k = 0; k < NCD; ++k) {
-                            s0 += gam[ab * NCD + k] * E3k[k][h];
-                            if (lr) s1 += gaml[ab * NCD + k] * E3k[k][h];
-                        }
-                        gr[h] = s0;
-                        grl[h] = s1;
-                    }
-                    float y[NH1P];
-#pragma unroll
-                    for (int h = 0; h < NH1P; ++h) y[h] = 0.0f;
-#pragma unroll 1
-                    for (int t2 = 0; t2 <= L2; ++t2)
-#pragma unroll 1
-                        for (int u2 = 0; u2 <= L2 - t2; ++u2)
-#pragma unroll 1
-                            for (int v2 = 0; v2 <= L2 - t2 - u2; ++v2) {
-                                const int h2 = hidx(t2, u2, v2);
-                                const float sg = ((t2 + u2 + v2) & 1) ? -1.0f : 1.0f;
-                                const float c0 = sg * gr[h2], c1 = sg * grl[h2];
-#pragma unroll
-                                for (int t1 = 0; t1 <= L1 + 1; ++t1)
-#pragma unroll
-                                    for (int u1 = 0; u1 <= L1 + 1 - t1; ++u1)
-#pragma unroll
-                                        for (int v1 = 0; v1 <= L1 + 1 - t1 - u1; ++v1) {
-                                            const int hr = hidx(t1 + t2, u1 + u2, v1 + v2);
-                                            float acc = y[hidx(t1, u1, v1)] + c0 * R[hr];
-                                            if (lr) acc += c1 * Rl[hr];
-                                            y[hidx(t1, u1, v1)] = acc;
-                                        }
-                            }
-#pragma unroll
-                    for (int t1 = 0; t1 <= L1 + 1; ++t1)
-#pragma unroll
-                        for (int u1 = 0; u1 <= L1 + 1 - t1; ++u1)
-#pragma unroll
-                            for (int v1 = 0; v1 <= L1 + 1 - t1 - u1; ++v1) y[hidx(t1, u1, v1)] *= spow[t1 + u1 + v1];
-                    const int nx = ax + bx, ny = ay + by, nz = az + bz;
-                    float sz[L1 + 2][L1 + 2];
-                    for (int t = 0; t <= nx + 1; ++t)
-                        for (int u = 0; u <= ny + 1 && t + u <= L1 + 1; ++u) {
-                            float acc = 0.0f;
-                            for (int v = 0; v <= nz && t + u + v <= L1 + 1; ++v) acc += Ebz[az][bz][v] * y[hidx(t, u, v)];
-                            sz[t][u] = acc;
-                        }
-                    float ax_ = 0.f, ay_ = 0.f, az_ = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
-                    for (int t = 0; t <= nx + 1; ++t) {
-                        const float dxt = za2 * Ebx[ax + 1][bx][t] - (ax > 0 ? ax * Ebx[ax - 1][bx][t] : 0.0f);
-                        float s = 0.0f;
-                        for (int u = 0; u <= ny; ++u) s += Eby[ay][by][u] * sz[t][u];
-                        ax_ += dxt * s;
-                    }
-                    for (int t = 0; t <= nx; ++t) {
-                        const float ext = Ebx[ax][bx][t];
-                        float sy = 0.f, sx1 = 0.f, sy1 = 0.f, szd = 0.f, sz1 = 0.f;
-                        for (int u = 0; u <= ny + 1; ++u) {
-                            const float dyu = za2 * Eby[ay + 1][by][u] - (ay > 0 ? ay * Eby[ay - 1][by][u] : 0.0f);
-                            sy += dyu * sz[t][u];
-                        }
-                        for (int u = 0; u <= ny; ++u) {
-                            const float eyu = Eby[ay][by][u];
-                            sx1 += eyu * sz[t + 1][u];
-                            sy1 += eyu * sz[t][u + 1];
-                            float a1 = 0.f, a2 = 0.f;
-                            for (int v = 0; v <= nz + 1; ++v) {
-                                const float dzv = za2 * Ebz[az + 1][bz][v] - (az > 0 ? az * Ebz[az - 1][bz][v] : 0.0f);
-                                a1 += dzv * y[hidx(t, u, v)];
-                            }
-                            for (int v = 0; v <= nz; ++v) a2 += Ebz[az][bz][v] * y[hidx(t, u, v + 1)];
-                            szd += eyu * a1;
-                            sz1 += eyu * a2;
-                        }
-                        ay_ += ext * sy;
-                        az_ += ext * szd;
-                        tx += ext * sx1;
-                        ty += ext * sy1;
-                        tz += ext * sz1;
-                    }
-                    fA[0] += ax_;
-                    fA[1] += ay_;
-                    fA[2] += az_;
-                    fT[0] += tx;
-                    fT[1] += ty;
-                    fT[2] += tz;
-                    ++ab;
-                });
-            }
-
-            {
-                int cd = 0;
-                for_pairs<LC, LD, UCD>([&](int cx, int cy, int cz, int dx, int dy, int dz) {
-                    float z[NH2P];
-#pragma unroll
-                    for (int h = 0; h < NH2P; ++h) z[h] = 0.0f;
-#pragma unroll 1
-                    for (int t1 = 0; t1 <= L1; ++t1)
-#pragma unroll 1
-                        for (int u1 = 0; u1 <= L1 - t1; ++u1)
-#pragma unroll 1
-                            for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
-                                const int h1 = hidx(t1, u1, v1);
-                                const float sh = spow[t1 + u1 + v1];
-                                const float f0 = Fa[cd][h1] * sh, f1 = Fl[cd][h1] * sh;
-#pragma unroll
-                                for (int t2 = 0; t2 <= L2 + 1; ++t2)
-#pragma unroll
-                                    for (int u2 = 0; u2 <= L2 + 1 - t2; ++u2)
-#pragma unroll
-                                        for (int v2 = 0; v2 <= L2 + 1 - t2 - u2; ++v2) {
-                                            const int hr = hidx(t1 + t2, u1 + u2, v1 + v2);
-                                            float acc = z[hidx(t2, u2, v2)] + f0 * R[hr];
-                                            if (lr) acc += f1 * Rl[hr];
-                                            z[hidx(t2, u2, v2)] = acc;
-                                        }
-                            }
-                    const int nx = cx + dx, ny = cy + dy, nz = cz + dz;
-#pragma unroll
-                    for (int t2 = 0; t2 <= L2 + 1; ++t2)
-#pragma unroll
-                        for (int u2 = 0; u2 <= L2 + 1 - t2; ++u2)
-#pragma unroll
-                            for (int v2 = 0; v2 <= L2 + 1 - t2 - u2; ++v2) {
-                                const float w = spow[t2 + u2 + v2];
-                                z[hidx(t2, u2, v2)] *= ((t2 + u2 + v2) & 1) ? -w : w;
-                            }
-                    float sz[L2 + 2][L2 + 2];
-                    for (int t = 0; t <= nx + 1; ++t)
-                        for (int u = 0; u <= ny + 1 && t + u <= L2 + 1; ++u) {
-                            float acc = 0.0f;
-                            for (int v = 0; v <= nz && t + u + v <= L2 + 1; ++v) acc += Ekz[cz][dz][v] * z[hidx(t, u, v)];
-                            sz[t][u] = acc;
-                        }
-                    float cx_ = 0.f, cy_ = 0.f, cz_ = 0.f;
-                    for (int t = 0; t <= nx + 1; ++t) {
-                        const float dxt = zc2 * Ekx[cx + 1][dx][t] - (cx > 0 ? cx * Ekx[cx - 1][dx][t] : 0.0f);
-                        float s = 0.0f;
-                        for (int u = 0; u <= ny; ++u) s += Eky[cy][dy][u] * sz[t][u];
-                        cx_ += dxt * s;
-                    }
-                    for (int t = 0; t <= nx; ++t) {
-                        const float ext = Ekx[cx][dx][t];
-                        float sy = 0.f, szd = 0.f;
-                        for (int u = 0; u <= ny + 1; ++u) {
-                            const float dyu = zc2 * Eky[cy + 1][dy][u] - (cy > 0 ? cy * Eky[cy - 1][dy][u] : 0.0f);
-                            sy += dyu * sz[t][u];
-                        }
-                        for (int u = 0; u <= ny; ++u) {
-                            float a1 = 0.f;
-                            for (int v = 0; v <= nz + 1; ++v) {
-                                const float dzv = zc2 * Ekz[cz + 1][dz][v] - (cz > 0 ? cz * Ekz[cz - 1][dz][v] : 0.0f);
-                                a1 += dzv * z[hidx(t, u, v)];
-                            }
-                            szd += Eky[cy][dy][u] * a1;
-                        }
-                        cy_ += ext * sy;
-                        cz_ += ext * szd;
-                    }
-                    fC[0] += cx_;
-                    fC[1] += cy_;
-                    fC[2] += cz_;
-                    ++cd;
-                });
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            gA[i] += (double)fA[i];
-            gC[i] += (double)fC[i];
-            gT[i] += (double)fT[i];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        g[i] = gA[i];
-        g[3 + i] = gT[i] - gA[i];
-        g[6 + i] = gC[i];
-        g[9 + i] = -gT[i] - gC[i];
-    }
-}
-
-// fp32 quartet, register-resident form.  Same algebra and scaled Hermite
-// basis as quartet_fp32, organised so the R tensor, the G row, y and z of
+// with X s, so every intermediate stays within fp32 range for any exponent;
+// the factors s^{|h|} are moved onto the short Hermite vectors (G rows,
+// F rows, y, z) and each bra primitive's contribution is added in fp64.
+// Register-resident form: the R tensor, the G row, y and z of
 // the current component pair stay in registers: the two operators are
 // processed one after the other (one R tensor live at a time), the Hermite
 // loops are fully unrolled, and only Gamma / F / E3k rows are read from
@@ -768,8 +447,8 @@ __device__ void quartet_fp32(const GeoArgs &geo, const DensArgs &den, const Prim
 // products use 1-D rows of the current component pair, zero beyond range.
 template <int LA, int LB, int LC, int LD>
 __device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp, int sa, int sb, int sc,
-                              int sd, int pb0, int nbp, int pk0, int nkp, double scale, const double *boys,
-                              double (&g)[12])
+                              int sd, int pb0, int nbp, int ib0, int ibs, int pk0, int nkp, double scale,
+                              const double *boys, double (&g)[12])
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int NAB = NA * NB, NCD = NC * ND;
@@ -795,7 +474,7 @@ __device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const Pri
     const long long nr = pp.n;
     double gA[3] = {0, 0, 0}, gC[3] = {0, 0, 0}, gT[3] = {0, 0, 0};
 
-    for (int ib = 0; ib < nbp; ++ib) {
+    for (int ib = ib0; ib < nbp; ib += ibs) {
         const int ip = pb0 + ib;
         const float pf = pp.fp[ip], Kab = pp.fK[ip];
         const float PAx = pp.fPA[ip], PAy = pp.fPA[nr + ip], PAz = pp.fPA[2 * nr + ip];
@@ -1096,8 +775,12 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
     double *slab = out.partials + (size_t)blockIdx.x * out.natom_total * 3;
     int cur = -1, cur_off3 = 0, cur_n3 = 0;
     unsigned long long nq = 0, npq = 0;
-    for (long long it = blockIdx.x; it < cl.ntiles; it += gridDim.x) {
-        const uint4 tl = cl.tiles[it];
+    // unit = (tile, split): split s takes the bra primitive pairs s, s + S, ...
+    const int S = cl.nsplit;
+    for (long long it = blockIdx.x; it < cl.ntiles * S; it += gridDim.x) {
+        const long long tile = it / S;
+        const int split = (int)(it % S);
+        const uint4 tl = cl.tiles[tile];
         const int mol = (int)tl.x;
         if (mol != cur) {
             if (out.use_smem) {
@@ -1124,6 +807,7 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
         for (int k = 0; k < 12; ++k) g[k] = 0.0;
         int at[4] = {-1, -1, -1, -1};
         bool ok = bi < bra.n && ki < ket.n && (!same || bi >= ki);
+        if (ok) ok = split < bra.np[bi];
         if (ok) {
             const int sa = bra.sa[bi], sb = bra.sb[bi], sc = ket.sa[ki], sd = ket.sb[ki];
             ok = keep_quartet(scr, bra, ket, bi, ki, sa, sb, sc, sd);
@@ -1134,21 +818,21 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
                 if (same && bi == ki) scale *= 0.5;
                 const int nbp = bra.np[bi], nkp = ket.np[ki];
                 if constexpr (FP32)
-                    quartet_fp32r<LA, LB, LC, LD>(geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi], nbp, ket.poff[ki],
-                                                  nkp, scale, boys, g);
+                    quartet_fp32r<LA, LB, LC, LD>(geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi], nbp, split, S,
+                                                  ket.poff[ki], nkp, scale, boys, g);
                 else
-                    quartet_fp64<LA, LB, LC, LD>(geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi], nbp, ket.poff[ki],
-                                                 nkp, scale, boys, g);
+                    quartet_fp64<LA, LB, LC, LD>(geo, md.den, pp, sa, sb, sc, sd, bra.poff[bi], nbp, split, S,
+                                                 ket.poff[ki], nkp, scale, boys, g);
                 at[0] = geo.sh_atom[sa];
                 at[1] = geo.sh_atom[sb];
                 at[2] = geo.sh_atom[sc];
                 at[3] = geo.sh_atom[sd];
-                nq += 1;
-                npq += (unsigned long long)nbp * nkp;
+                if (split == 0) nq += 1;
+                npq += (unsigned long long)((nbp - split + S - 1) / S) * nkp;
             }
         }
-        if (out.dump) {
-            double *d = out.dump + ((size_t)it * TILE + threadIdx.x) * 12;
+        if (out.dump) {  // dump mode runs with one split per tile
+            double *d = out.dump + ((size_t)tile * TILE + threadIdx.x) * 12;
 #pragma unroll
             for (int k = 0; k < 12; ++k) d[k] = g[k];
             continue;
@@ -1169,22 +853,51 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
         nq += __shfl_xor_sync(0xffffffffu, nq, o);
         npq += __shfl_xor_sync(0xffffffffu, npq, o);
     }
-    if ((threadIdx.x & 31) == 0 && nq) {
+    if ((threadIdx.x & 31) == 0 && (nq || npq)) {  // a split unit may hold primitives only
         atomicAdd(out.counters + 0, nq);
         atomicAdd(out.counters + (FP32 ? 3 : 1), npq);
         if (FP32) atomicAdd(out.counters + 2, nq);
     }
 }
 
+// Launch of a persistent class kernel over units: the grid is the smaller of
+// gcap and the kernel's resident CTAs per SM times the SM count, and each
+// tile is cut into nchunk x nsplit units (nchunk only for the cooperative
+// kernel, whose CTA holds ngroups quartets at a time) until there are at
+// least four units per CTA, so that classes with few tiles still fill the
+// GPU.  Dump mode keeps one unit per tile.
+template <typename K>
+cudaError_t launch_units(K kern, int ngroups, int gcap, size_t sm, cudaStream_t st, const MolDesc *mols,
+                         ClassLaunch cl, const OutArgs &out, const double *boys)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 1, per = 1;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TILE, sm)) != cudaSuccess) return e;
+    long long gmax = (long long)(per > 0 ? per : 1) * nsm;
+    if (gmax > gcap) gmax = gcap;
+    cl.nchunk = 1;
+    cl.nsplit = 1;
+    if (!out.dump) {
+        const long long want = 4 * gmax;
+        if (ngroups > 0)
+            while (cl.ntiles * cl.nchunk < want && cl.nchunk * ngroups < TILE) cl.nchunk *= 2;
+        while (cl.ntiles * cl.nchunk * cl.nsplit < want && cl.nsplit < 4) ++cl.nsplit;
+    }
+    const long long units = cl.ntiles * cl.nchunk * cl.nsplit;
+    const int grid = (int)(units < gmax ? units : gmax);
+    kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
+    return cudaGetLastError();
+}
+
 template <int LA, int LB, int LC, int LD>
-cudaError_t launch_thread_kernel(int fp32, int grid, size_t smem, cudaStream_t st, const MolDesc *mols,
+cudaError_t launch_thread_kernel(int fp32, int gcap, size_t smem, cudaStream_t st, const MolDesc *mols,
                                  const ClassLaunch &cl, const OutArgs &out, const double *boys)
 {
-    auto kern = fp32 ? k_grad<LA, LB, LC, LD, true> : k_grad<LA, LB, LC, LD, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, TILE, smem, st>>>(mols, cl, out, boys);
-    return cudaGetLastError();
+    if (fp32) return launch_units(k_grad<LA, LB, LC, LD, true>, 0, gcap, smem, st, mols, cl, out, boys);
+    return launch_units(k_grad<LA, LB, LC, LD, false>, 0, gcap, smem, st, mols, cl, out, boys);
 }
 
 }  // namespace tg

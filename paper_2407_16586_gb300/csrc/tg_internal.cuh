@@ -94,6 +94,9 @@ struct ClassLaunch {
     int P, Q;                  // bra and ket pair classes (same list iff P == Q)
     long long ntiles;
     const uint4 *tiles;        // (molecule, bra tile, ket tile, 0), grouped by molecule
+    int nsplit;                // units per tile along the bra primitive pairs (>= 1)
+    int nchunk;                // cooperative kernel: quartet chunks per tile (divides TILE / groups)
+    int kind;                  // 0: default kernel of the class, 1: thread kernel, 2: cooperative kernel
 };
 
 struct OutArgs {

@@ -11,7 +11,13 @@ two constants on held-out tiles:
 
 TG_MIXED_LEARNED then sends tiles to fp32 in increasing order of
 e_t = eps_rel * 10^(prediction + margin) while sum e_t^2 <= (mixed_tol/3)^2
-(mixed_tol defaults to 1e-6 Ha/bohr)."""
+(mixed_tol defaults to 1e-6 Ha/bohr).
+
+Both percentiles bound single tiles, so the summed estimate overstates the
+error of the routed set by orders of magnitude.  calibrate_budget() then
+measures the whole route: on held-out molecules it runs the mixed path
+against fp64 while lowering the margin in steps of 0.5 (log10), and keeps
+the lowest margin whose largest max|dg| stays within mixed_tol / safety."""
 from __future__ import annotations
 
 import numpy as np
@@ -51,3 +57,35 @@ def fit(X, y, e, seed=7, epochs=400, lr=1e-2, q=0.9, holdout=0.2, floor=-20.0):
     info = dict(n_train=len(tr), n_hold=nh, loss_first=float(hist[0]), loss_last=float(hist[-1]), margin=margin,
                 eps_rel=eps_rel, resid_hold_mean=float(np.mean(y[hold] - pred)))
     return r, info
+
+
+def calibrate_budget(r, systems, mixed_tol=1e-6, safety=5.0, step=0.5, max_steps=16, screen_tol=1e-10):
+    """Lower the router's margin while the measured max|dg| of TG_MIXED_LEARNED
+    against TG_FP64 over ``systems`` stays <= mixed_tol / safety.  Returns a
+    list of (margin, max error, fp32 quartet fraction) for every margin tried."""
+    params, mu, sd, calib = r.get()
+    margin0, eps_rel = float(calib[0]), float(calib[1])
+    runs = []
+    for s in systems:
+        b = tg.Basis(s)
+        g64, _ = b.grad2e(s["pairs"], screen_tol=screen_tol)
+        runs.append((b, s, g64))
+    best, log = margin0, []
+    for k in range(max_steps + 1):
+        m = margin0 - step * k
+        r.set(calib=[m, eps_rel, 1.0])
+        err, q32, q = 0.0, 0, 0
+        for b, s, g64 in runs:
+            g, st = b.grad2e(s["pairs"], screen_tol=screen_tol, precision=tg.TG_MIXED_LEARNED, router=r,
+                             mixed_tol=mixed_tol)
+            err = max(err, float(np.abs(g - g64).max()))
+            q32 += st["fp32_quartets"]
+            q += st["quartets"]
+        log.append((m, err, q32 / max(q, 1)))
+        if err > mixed_tol / safety:
+            break
+        best = m
+    r.set(calib=[best, eps_rel, 1.0])
+    for b, _, _ in runs:
+        b.close()
+    return log

@@ -6,7 +6,11 @@
 Every cluster comes from synth.router_cluster(i) (seed 20240716 + i); every
 stride-th screened quartet tile of each is evaluated in fp64 and fp32
 (tg_tile_samples), the MLP is trained on the GPU (tg_router_train) and the
-margin / eps_rel calibration is taken on 20 % held-out tiles."""
+margin / eps_rel calibration is taken on 20 % held-out tiles; the margin is
+then lowered on a budget set (--budget-clusters clusters and --budget-chains
+chains) while the measured error of the whole mixed route stays within a
+fifth of mixed_tol (router.calibrate_budget).  --recalibrate FILE keeps FILE's network and
+redoes only that last step."""
 import argparse
 import json
 import os
@@ -23,12 +27,31 @@ def main():
     ap.add_argument("--cap", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "router.bin"))
+    ap.add_argument("--budget-clusters", type=int, default=2)
+    ap.add_argument("--budget-natom", type=int, default=24)
+    ap.add_argument("--budget-chains", type=int, default=2, help="20-atom chains added to the budget set")
+    ap.add_argument("--budget-first", type=int, default=100000, help="first cluster index of the budget set")
+    ap.add_argument("--recalibrate", default=None, help="router file whose network is kept")
     args = ap.parse_args()
     from paper_2407_16586_gb300 import build
     build.build()
     import paper_2407_16586_gb300 as tg
     from paper_2407_16586_gb300 import router, synth
     t0 = time.time()
+    # budget set: compact clusters and chains (seeds unrelated to the workloads)
+    budget_set = [synth.router_cluster(i, natom=args.budget_natom)
+                  for i in range(args.budget_first, args.budget_first + args.budget_clusters)]
+    budget_set += [synth.molecule(args.budget_first + i, 8, 12) for i in range(args.budget_chains)]
+    if args.recalibrate:
+        r = tg.Router(path=args.recalibrate)
+        info = dict(recalibrated_from=os.path.basename(args.recalibrate))
+        info["budget_log"] = router.calibrate_budget(r, budget_set)
+        info["margin"] = float(r.get()[3][0])
+        r.save(args.out)
+        with open(args.out + ".json", "w") as f:
+            json.dump(info, f, indent=1)
+        print(json.dumps(info))
+        return
     Xs, ys, es = [], [], []
     for i in range(args.first, args.first + args.clusters):
         s = synth.router_cluster(i)
@@ -39,6 +62,8 @@ def main():
     X, y, e = np.concatenate(Xs), np.concatenate(ys), np.concatenate(es)
     t1 = time.time()
     r, info = router.fit(X, y, e, epochs=args.epochs)
+    info["budget_log"] = router.calibrate_budget(r, budget_set)
+    info["margin"] = float(r.get()[3][0])
     r.save(args.out)
     info.update(clusters=args.clusters, stride=args.stride, tiles=int(len(y)), sample_s=t1 - t0,
                 train_s=time.time() - t1)

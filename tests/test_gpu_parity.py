@@ -41,6 +41,22 @@ def test_small_molecules(tg, seed, nheavy, nh):
     assert np.abs(g - ref).max() <= TOL
 
 
+def test_kernel_kinds(tg):
+    """Both class-kernel forms (one quartet per thread; a thread group per
+    quartet, with tiles cut into quartet chunks and bra-primitive splits) give
+    the oracle's gradient, and the same quartet and primitive-quartet counts."""
+    s = synth.molecule(14, 3, 3)
+    b = tg.Basis(s)
+    ref, _, nq = oracle.grad2e(s, tau=0.0)
+    pqs = []
+    for kernel in (1, 2):
+        g, st = b.grad2e(s["pairs"], screen_tol=0.0, kernel=kernel)
+        assert st["quartets"] == nq
+        assert np.abs(g - ref).max() <= TOL, (kernel, np.abs(g - ref).max())
+        pqs.append(st["prim_quartets"])
+    assert pqs[0] == pqs[1]
+
+
 def test_screening_follows_the_defined_bound(tg, c1):
     for tau in (1e-10, 1e-7, 1e-4):
         g, st = tg.grad2e(c1, screen_tol=tau)

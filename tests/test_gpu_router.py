@@ -78,6 +78,12 @@ def test_learned_router_gain_over_bound_router(tg):
     assert np.abs(gb - g64).max() <= 1e-6
     assert np.abs(gl - g64).max() <= 1e-6
     assert sl["fp32_quartets"] > sb["fp32_quartets"]
+    # measured budget calibration on another molecule: more fp32, still within tolerance
+    log = router.calibrate_budget(r, [synth.router_cluster(50, natom=20)], safety=10.0, max_steps=8)
+    assert log[0][1] <= 1e-6 / 10
+    g2, s2 = b.grad2e(s["pairs"], screen_tol=1e-10, precision=tg.TG_MIXED_LEARNED, router=r)
+    assert np.abs(g2 - g64).max() <= 1e-6
+    assert s2["fp32_quartets"] >= sl["fp32_quartets"]
 
 
 def test_learned_mode_needs_a_trained_router(tg, c1):
