@@ -31,6 +31,14 @@ TAU = 1e-10
 L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
 # FLOPs per primitive quartet of the MD-GF algorithm (FMA = 2), see the design doc.
+# DRAM bytes per primitive quartet of a class kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over the kernel's primitive
+# quartets) on the 12-atom chain "chain:5:6:6"; the bench scales it to the
+# launch it times.  Keyed by (kernel kind, class, fp32); profiles/ holds the
+# capture.  An entry is removed when its kernel changes.
+TRAFFIC_PER_PQ = {("thread", (2, 1, 1, 1), False): 10.019916e9 / 521142}
+
+
 def _nherm(L):
     return 0 if L < 0 else (L + 1) * (L + 2) * (L + 3) // 6
 
@@ -318,7 +326,8 @@ def main():
         pk = peaks["fp32" if fp32 else "fp64"]
         nc = lambda l: (l + 1) * (l + 2) // 2
         nfq = nc(la) * nc(lb) * nc(lc) * nc(ld)
-        coop = nfq >= (648 if fp32 else 216)  # the library's default kernel per class
+        # the library's default kernel per class
+        coop = nfq >= 648 if fp32 else (nfq >= 216 or (la, lb, lc, ld) == (2, 1, 2, 0))
         kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if coop else "",
                                                names[la], names[lb], names[lc], names[ld],
                                                "fp32" if fp32 else "fp64")
@@ -338,7 +347,10 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                         "frac": achieved / pk, "traffic": None,
+                         "frac": achieved / pk,
+                         "traffic": (TRAFFIC_PER_PQ[("coop" if coop else "thread", (la, lb, lc, ld), fp32)] * npq
+                                     if ("coop" if coop else "thread", (la, lb, lc, ld), fp32) in TRAFFIC_PER_PQ
+                                     else None),
                          "peak_source": "derived: 152 SM x (2 fp64 | 128 fp32) FMA/clk x 2 flop x 2.07 GHz",
                          "kernel_ms": ms, "kernel_prim_quartets": npq,
                          "all_kernels_tflops": tot_flops / (tot_ms / 1e3) / 1e12 if tot_ms > 0 else None},

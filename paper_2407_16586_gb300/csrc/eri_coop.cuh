@@ -1,12 +1,22 @@
 // Cooperative derivative-ERI class kernel for the large angular classes.
 //
-// Same algebra as quartet_fp64 / quartet_fp32 (eri_grad.cuh), but a group of
-// GS threads shares one contracted quartet and every array lives in shared
-// memory: Gamma, the F rows (per bra primitive pair), the ket Hermite
-// products, the R tensors, the G rows, and y / z.  Each phase is split over
-// (function pair, Hermite index) items, so a d-shell quartet keeps all GS
-// threads busy without spilling to local memory.  In fp32 the scaled Hermite
-// basis R'_h = R_h / s^{|h|}, s = sqrt(2 rho), keeps values in range.
+// Same integrals and density contraction as quartet_fp64 / quartet_fp32r
+// (eri_grad.cuh), reorganised for a group of GS threads that shares one
+// contracted quartet, with every array in shared memory.  Per bra primitive
+// pair p and ket primitive pair q (both operators s = full, lr):
+//
+//   W_s[cd][h1] += sum_h2 (-1)^|h2| E^{cd}_{h2}(q) R_s[h1+h2](p,q)    (over q)
+//   z[cd][h2]    = (-1)^|h2| sum_s sum_h1 F_s[cd][h1](p) R_s[h1+h2](p,q)
+//   d/dC        += sum_{cd,h2} dE^{cd}_{h2}/dC (q) z[cd][h2]
+//
+// and after the ket loop Y[ab][h1] = sum_s sum_cd Gamma_s[ab][cd] W_s[cd][h1]
+// gives d/dA (with dE^{ab}/dA) and d/dA + d/dB (with E^{ab} and the shifted
+// index h1 + 1_x, the R-tensor shift of eq. deriv).  The bra-side density
+// contraction therefore happens once per bra primitive pair instead of once
+// per primitive quartet, and every phase is split over (function pair,
+// Hermite index) items so that all GS threads stay busy.  In fp32 the scaled
+// Hermite basis R'_h = R_h / s^{|h|}, s = sqrt(2 rho), keeps values in
+// range; the factors s^{|h|} go onto E^{cd}, W and z.
 #pragma once
 #include "eri_grad.cuh"
 
@@ -33,16 +43,14 @@ struct CoopLayout {
     // element offsets (in F units) of the per-group regions
     static constexpr int o_gam = 0;
     static constexpr int o_gaml = o_gam + NAB * NCD;
-    static constexpr int o_F = o_gaml + NAB * NCD;          // [2][NCD][NH1]
-    static constexpr int o_E3k = o_F + 2 * NCD * NH1;       // [NCD][NH2]
+    static constexpr int o_F = o_gaml + NAB * NCD;          // [2][NCD][NH1], per bra primitive pair
+    static constexpr int o_E3b = o_F + 2 * NCD * NH1;       // [NAB][NH1], per bra primitive pair
+    static constexpr int o_W = o_E3b + NAB * NH1;           // [2][NCD][NH1P], summed over ket primitives
+    static constexpr int o_E3k = o_W + 2 * NCD * NH1P;      // [NCD][NH2]
     static constexpr int S = L + 2;                         // dense-cube stride of R
     static constexpr int NCUBE = S * S * S;
     static constexpr int o_R = o_E3k + NCD * NH2;           // [2][S^3] dense R cubes (+ 2 * (L+2) bases)
-    static constexpr int o_G = o_R + 2 * NCUBE + 2 * (L + 2);  // [2][NAB][NH2]; E3b [NAB][NH1] aliases it
-    static constexpr int GSZ = 2 * NAB * NH2 > NAB * NH1 ? 2 * NAB * NH2 : NAB * NH1;
-    static constexpr int o_YZ = o_G + GSZ;                  // y [NAB][NH1P] or z [NCD][NH2P]
-    static constexpr int YZ = NAB * NH1P > NCD * NH2P ? NAB * NH1P : NCD * NH2P;
-    static constexpr int o_Eb = o_YZ + YZ;                  // 3 x NEB
+    static constexpr int o_Eb = o_R + 2 * NCUBE + 2 * (L + 2);  // 3 x NEB
     static constexpr int o_Ek = o_Eb + 3 * NEB;             // 3 x NEK
     static constexpr int o_sc = o_Ek + 3 * NEK;             // scalars and powers of s
     static constexpr int NSC = 16 + L + 3;
@@ -52,9 +60,34 @@ struct CoopLayout {
 
 __device__ __forceinline__ int ebi(int i, int j, int t, int J1, int T1) { return (i * J1 + j) * T1 + t; }
 
+// Hermite index h -> (t, u, v), the inverse of hidx.
+__device__ __forceinline__ void hdecode(int h, int &n, int &t, int &u, int &v)
+{
+    n = 0;
+    while (nherm(n) <= h) ++n;
+    const int r = h - nherm(n - 1);
+    int s = 0;
+    while ((s + 1) * (s + 2) / 2 <= r) ++s;
+    v = r - s * (s + 1) / 2;
+    u = s - v;
+    t = n - s;
+}
+
+// Cartesian component c of a shell of angular momentum l -> exponents
+// (lexicographic order xx, xy, xz, yy, yz, zz).
+__device__ __forceinline__ void cdecode(int c, int l, int &x, int &y, int &z)
+{
+    int s = 0;
+    while ((s + 1) * (s + 2) / 2 <= c) ++s;
+    z = c - s * (s + 1) / 2;
+    y = s - z;
+    x = l - s;
+}
+
 // One contracted quartet by a group of GS threads (lane = thread index within
-// the group).  Returns d/dA, d/dP, d/dC partial sums of this lane; the caller
-// reduces them over the group.
+// the group), bra primitive pairs ib0, ib0 + ibs, ...  Adds this lane's
+// partial sums of d/dA (acc[0..2]), d/dA + d/dB (acc[3..5]) and d/dC
+// (acc[6..8]); the caller reduces them over the group.
 template <int LA, int LB, int LC, int LD, typename F, int GS>
 __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp,
                              int sa, int sb, int sc, int sd, int pb0, int nbp, int ib0, int ibs, int pk0, int nkp,
@@ -63,13 +96,14 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
     using Lay = CoopLayout<LA, LB, LC, LD, F>;
     constexpr int NB = Lay::NB, ND = Lay::ND, NAB = Lay::NAB, NCD = Lay::NCD;
     constexpr int L1 = Lay::L1, L2 = Lay::L2, L = Lay::L;
-    constexpr int NH1 = Lay::NH1, NH1P = Lay::NH1P, NH2 = Lay::NH2, NH2P = Lay::NH2P, NR = Lay::NR;
+    constexpr int NH1 = Lay::NH1, NH1P = Lay::NH1P, NH2 = Lay::NH2, NH2P = Lay::NH2P;
     constexpr int BJ = LB + 1, BT = L1 + 2, KJ = LD + 1, KT = L2 + 2;
+    constexpr int S = Lay::S, NCUBE = Lay::NCUBE;
     constexpr bool FP32 = sizeof(F) == 4;
-    F *gam = sm + Lay::o_gam, *gaml = sm + Lay::o_gaml, *Fr = sm + Lay::o_F, *E3k = sm + Lay::o_E3k;
-    F *Rb = sm + Lay::o_R, *G = sm + Lay::o_G, *YZ = sm + Lay::o_YZ, *Eb = sm + Lay::o_Eb, *Ek = sm + Lay::o_Ek;
+    F *gam = sm + Lay::o_gam, *gaml = sm + Lay::o_gaml, *Fr = sm + Lay::o_F, *E3b = sm + Lay::o_E3b;
+    F *W = sm + Lay::o_W, *E3k = sm + Lay::o_E3k, *Rb = sm + Lay::o_R, *Eb = sm + Lay::o_Eb, *Ek = sm + Lay::o_Ek;
     F *scl = sm + Lay::o_sc;
-    F *E3b = G;  // aliases G: only used while building the F rows
+    const F *spow = scl + 16;
     const bool lr = den.use_lr;
     const double om2 = den.omega * den.omega;
     const bool ominf = isinf(den.omega);
@@ -119,44 +153,20 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                     for (int t = 0; t <= L1 + 1; ++t) dst[ebi(i, j, t, BJ, BT)] = E[i][j][t];
         }
         group_sync(bar, GS);
-        // E3b[ab][h1] = E_x E_y E_z (zero outside each component's range)
+        // E3b[ab][h1] = E_x E_y E_z (zero outside each component's range); W = 0
         for (int it = lane; it < NAB * NH1; it += GS) {
             const int ab = it / NH1, h = it % NH1;
-            int t, u, v;
-            {
-                int n = 0;
-                while (nherm(n) <= h) ++n;
-                const int r = h - nherm(n - 1);
-                int s = 0;
-                while ((s + 1) * (s + 2) / 2 <= r) ++s;
-                v = r - s * (s + 1) / 2;
-                u = s - v;
-                t = n - s;
-            }
-            const int ma = ab / NB, mb = ab % NB;
-            int ax, ay, bx, by;
-            {
-                // component -> exponents (lexicographic order)
-                int c = ma, l = LA, s = 0;
-                while ((s + 1) * (s + 2) / 2 <= c) ++s;
-                const int lz = c - s * (s + 1) / 2;
-                ay = s - lz;
-                ax = l - s;
-                c = mb;
-                l = LB;
-                s = 0;
-                while ((s + 1) * (s + 2) / 2 <= c) ++s;
-                const int lz2 = c - s * (s + 1) / 2;
-                by = s - lz2;
-                bx = l - s;
-            }
-            const int az = LA - ax - ay, bz = LB - bx - by;
+            int n, t, u, v, ax, ay, az, bx, by, bz;
+            hdecode(h, n, t, u, v);
+            cdecode(ab / NB, LA, ax, ay, az);
+            cdecode(ab % NB, LB, bx, by, bz);
             F e = F(0);
             if (t <= ax + bx && u <= ay + by && v <= az + bz)
                 e = Eb[ebi(ax, bx, t, BJ, BT)] * Eb[Lay::NEB + ebi(ay, by, u, BJ, BT)] *
                     Eb[2 * Lay::NEB + ebi(az, bz, v, BJ, BT)];
             E3b[it] = e;
         }
+        for (int it = lane; it < 2 * NCD * NH1P; it += GS) W[it] = F(0);
         group_sync(bar, GS);
         // F_s[cd][h1] = sum_ab Gamma_s[ab][cd] E3b[ab][h1]
         for (int it = lane; it < NCD * NH1; it += GS) {
@@ -200,7 +210,7 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 const float th2 = (lane == 3) ? 1.0f : (ominf ? 1.0f : om2f / (om2f + rho));
                 float Fm[L + 2];
                 boys_mixed<L + 1>(T * th2, Fm, boys);
-                F *base = Rb + 2 * Lay::NCUBE + (lane - 3) * (L + 2);
+                F *base = Rb + 2 * NCUBE + (lane - 3) * (L + 2);
                 float f = pref * sqrtf(th2);
                 for (int n = 0; n <= L + 1; ++n) {
                     base[n] = (F)((n & 1) ? -f * Fm[n] : f * Fm[n]);
@@ -225,37 +235,17 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                 const double th2 = (lane == 3) ? 1.0 : (ominf ? 1.0 : om2 / (om2 + rho));
                 double Fm[L + 2];
                 boys_fp64<L + 1>(T * th2, Fm, boys);
-                F *base = Rb + 2 * Lay::NCUBE + (lane - 3) * (L + 2);
-                if (FP32) {
-                    // scaled basis: base'_n = pref theta (-theta^2)^n F_n, recursion with X s
-                    double f = pref * sqrt(th2);
-                    for (int n = 0; n <= L + 1; ++n) {
-                        base[n] = (F)((n & 1) ? -f * Fm[n] : f * Fm[n]);
-                        f *= th2;
-                    }
-                    if (lane == 3) {
-                        const double s = sqrt(2.0 * rho);
-                        scl[0] = (F)(X * s);
-                        scl[1] = (F)(Y * s);
-                        scl[2] = (F)(Z * s);
-                        F pw = F(1);
-                        for (int n = 0; n <= L + 2; ++n) {
-                            scl[16 + n] = pw;
-                            pw *= (F)s;
-                        }
-                    }
-                } else {
-                    double f = pref * sqrt(th2), m2 = -2.0 * rho * th2;
-                    for (int n = 0; n <= L + 1; ++n) {
-                        base[n] = (F)(f * Fm[n]);
-                        f *= m2;
-                    }
-                    if (lane == 3) {
-                        scl[0] = (F)X;
-                        scl[1] = (F)Y;
-                        scl[2] = (F)Z;
-                        for (int n = 0; n <= L + 2; ++n) scl[16 + n] = F(1);
-                    }
+                F *base = Rb + 2 * NCUBE + (lane - 3) * (L + 2);
+                double f = pref * sqrt(th2), m2 = -2.0 * rho * th2;
+                for (int n = 0; n <= L + 1; ++n) {
+                    base[n] = (F)(f * Fm[n]);
+                    f *= m2;
+                }
+                if (lane == 3) {
+                    scl[0] = (F)X;
+                    scl[1] = (F)Y;
+                    scl[2] = (F)Z;
+                    for (int n = 0; n <= L + 2; ++n) scl[16 + n] = F(1);
                 }
             }
             group_sync(bar, GS);
@@ -263,7 +253,6 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
             // level and, within a level, total by total from high to low, so
             // each entry reads level n+1 values (as in hermite_R)
             {
-                constexpr int S = Lay::S, NCUBE = Lay::NCUBE;
                 const F X = scl[0], Y = scl[1], Z = scl[2];
                 const int nops = lr ? 2 : 1;
                 const F *bases = Rb + 2 * NCUBE;
@@ -297,72 +286,31 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
                     group_sync(bar, GS);
                 }
             }
-            constexpr int S = Lay::S;
-            const F *R3 = Rb, *R3l = Rb + Lay::NCUBE;
-            const F *spow = scl + 16;
-            // ket products E3k[cd][h2] (times s^{|h2|} in fp32)
+            const F *R3 = Rb, *R3l = Rb + NCUBE;
+            // ket products E3k[cd][h2] = (-1)^|h2| E_x E_y E_z (times s^{|h2|} in fp32)
             for (int it = lane; it < NCD * NH2; it += GS) {
                 const int cd = it / NH2, h = it % NH2;
-                int n = 0;
-                while (nherm(n) <= h) ++n;
-                const int rr = h - nherm(n - 1);
-                int s = 0;
-                while ((s + 1) * (s + 2) / 2 <= rr) ++s;
-                const int v = rr - s * (s + 1) / 2, u = s - v, t = n - s;
-                const int mc = cd / ND, md = cd % ND;
-                int cx, cy, dx, dy;
-                {
-                    int c = mc, q = 0;
-                    while ((q + 1) * (q + 2) / 2 <= c) ++q;
-                    cy = q - (c - q * (q + 1) / 2);
-                    cx = LC - q;
-                    c = md;
-                    q = 0;
-                    while ((q + 1) * (q + 2) / 2 <= c) ++q;
-                    dy = q - (c - q * (q + 1) / 2);
-                    dx = LD - q;
-                }
-                const int cz = LC - cx - cy, dz = LD - dx - dy;
+                int n, t, u, v, cx, cy, cz, dx, dy, dz;
+                hdecode(h, n, t, u, v);
+                cdecode(cd / ND, LC, cx, cy, cz);
+                cdecode(cd % ND, LD, dx, dy, dz);
                 F e = F(0);
                 if (t <= cx + dx && u <= cy + dy && v <= cz + dz)
                     e = Ek[ebi(cx, dx, t, KJ, KT)] * Ek[Lay::NEK + ebi(cy, dy, u, KJ, KT)] *
                         Ek[2 * Lay::NEK + ebi(cz, dz, v, KJ, KT)] * spow[n];
-                E3k[it] = e;
+                E3k[it] = (n & 1) ? -e : e;
             }
             group_sync(bar, GS);
-            // G_s[ab][h2] = sum_cd Gamma_s[ab][cd] E3k[cd][h2], times (-1)^{|h2|}
-            for (int it = lane; it < NAB * NH2; it += GS) {
-                const int ab = it / NH2, h = it % NH2;
-                F s0 = F(0), s1 = F(0);
-                for (int cd = 0; cd < NCD; ++cd) {
-                    const F e = E3k[cd * NH2 + h];
-                    s0 += gam[ab * NCD + cd] * e;
-                    s1 += gaml[ab * NCD + cd] * e;
-                }
-                int n = 0;
-                while (nherm(n) <= h) ++n;
-                if (n & 1) {
-                    s0 = -s0;
-                    s1 = -s1;
-                }
-                G[it] = s0;
-                G[NAB * NH2 + it] = s1;
-            }
-            group_sync(bar, GS);
-            // y[ab][h1] = sum_h2 G[ab][h2] R[h1+h2] (+ lr), times s^{|h1|}; the
-            // cube index of h1+h2 is base(h1) + off(h2) with off a constant of
-            // the unrolled h2 loop
-            for (int it = lane; it < NAB * NH1P; it += GS) {
-                const int ab = it / NH1P, h1 = it % NH1P;
-                int n1 = 0;
-                while (nherm(n1) <= h1) ++n1;
-                const int r1 = h1 - nherm(n1 - 1);
-                int s1 = 0;
-                while ((s1 + 1) * (s1 + 2) / 2 <= r1) ++s1;
-                const int v1 = r1 - s1 * (s1 + 1) / 2, u1 = s1 - v1, t1 = n1 - s1;
+            // W_s[cd][h1] += s^{|h1|} sum_h2 E3k[cd][h2] R_s[h1+h2]; the cube
+            // index of h1+h2 is base(h1) + off(h2), off a constant of the
+            // unrolled h2 loop
+            for (int it = lane; it < NCD * NH1P; it += GS) {
+                const int cd = it / NH1P, h1 = it % NH1P;
+                int n1, t1, u1, v1;
+                hdecode(h1, n1, t1, u1, v1);
                 const int b1 = (t1 * S + u1) * S + v1;
-                const F *g0 = G + ab * NH2, *g1 = G + NAB * NH2 + ab * NH2;
-                F y0 = F(0), y1 = F(0);
+                const F *e = E3k + cd * NH2;
+                F w0 = F(0), w1 = F(0);
 #pragma unroll
                 for (int t2 = 0; t2 <= L2; ++t2)
 #pragma unroll
@@ -370,135 +318,70 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
 #pragma unroll
                         for (int v2 = 0; v2 <= L2 - t2 - u2; ++v2) {
                             const int off = (t2 * S + u2) * S + v2;
-                            y0 += g0[hidx(t2, u2, v2)] * R3[b1 + off];
-                            if (lr) y1 += g1[hidx(t2, u2, v2)] * R3l[b1 + off];
+                            const F ev = e[hidx(t2, u2, v2)];
+                            w0 += ev * R3[b1 + off];
+                            if (lr) w1 += ev * R3l[b1 + off];
                         }
-                F y = y0 + y1;
-                if constexpr (FP32) y *= spow[n1];
-                YZ[it] = y;
-            }
-            group_sync(bar, GS);
-            // d/dA and d/dP per bra component pair
-            for (int ab = lane; ab < NAB; ab += GS) {
-                const int ma = ab / NB, mb = ab % NB;
-                int ax, ay, bx, by;
-                {
-                    int c = ma, q = 0;
-                    while ((q + 1) * (q + 2) / 2 <= c) ++q;
-                    ay = q - (c - q * (q + 1) / 2);
-                    ax = LA - q;
-                    c = mb;
-                    q = 0;
-                    while ((q + 1) * (q + 2) / 2 <= c) ++q;
-                    by = q - (c - q * (q + 1) / 2);
-                    bx = LB - q;
+                if constexpr (FP32) {
+                    w0 *= spow[n1];
+                    w1 *= spow[n1];
                 }
-                const int az = LA - ax - ay, bz = LB - bx - by;
-                const F za2 = (F)(2.0 * pp.za[ip]);
-                const F *y = YZ + ab * NH1P;
-                const F *Ex = Eb, *Ey = Eb + Lay::NEB, *Ez = Eb + 2 * Lay::NEB;
-                const int nx = ax + bx, ny = ay + by, nz = az + bz;
-                F a0 = 0, a1 = 0, a2 = 0, t0 = 0, t1 = 0, t2 = 0;
-                for (int t = 0; t <= nx + 1; ++t) {
-                    const F ex = t <= nx ? Ex[ebi(ax, bx, t, BJ, BT)] : F(0);
-                    const F dxv = za2 * Ex[ebi(ax + 1, bx, t, BJ, BT)] - (ax > 0 ? F(ax) * Ex[ebi(ax - 1, bx, t, BJ, BT)] : F(0));
-                    for (int u = 0; u <= ny + 1; ++u) {
-                        const F ey = u <= ny ? Ey[ebi(ay, by, u, BJ, BT)] : F(0);
-                        const F dyv = za2 * Ey[ebi(ay + 1, by, u, BJ, BT)] - (ay > 0 ? F(ay) * Ey[ebi(ay - 1, by, u, BJ, BT)] : F(0));
-                        for (int v = 0; v <= nz + 1; ++v) {
-                            if (t + u + v > L1 + 1) continue;
-                            const F ez = v <= nz ? Ez[ebi(az, bz, v, BJ, BT)] : F(0);
-                            const F dzv = za2 * Ez[ebi(az + 1, bz, v, BJ, BT)] - (az > 0 ? F(az) * Ez[ebi(az - 1, bz, v, BJ, BT)] : F(0));
-                            const F yy = y[hidx(t, u, v)];
-                            if (u <= ny && v <= nz) a0 += dxv * ey * ez * yy;
-                            if (t <= nx && v <= nz) a1 += ex * dyv * ez * yy;
-                            if (t <= nx && u <= ny) a2 += ex * ey * dzv * yy;
-                            if (t <= nx && u <= ny && v <= nz) {
-                                const F e3 = ex * ey * ez;
-                                t0 += e3 * y[hidx(t + 1, u, v)];
-                                t1 += e3 * y[hidx(t, u + 1, v)];
-                                t2 += e3 * y[hidx(t, u, v + 1)];
-                            }
-                        }
-                    }
-                }
-                acc[0] += (double)a0;
-                acc[1] += (double)a1;
-                acc[2] += (double)a2;
-                acc[3] += (double)t0;
-                acc[4] += (double)t1;
-                acc[5] += (double)t2;
+                W[it] += w0;
+                if (lr) W[NCD * NH1P + it] += w1;
             }
-            group_sync(bar, GS);
-            // z[cd][h2] = sum_h1 F[cd][h1] s^{|h1|} R[h1+h2] (+ lr), times (-1)^{|h2|} s^{|h2|}
-            for (int it = lane; it < NCD * NH2P; it += GS) {
-                const int cd = it / NH2P, h2 = it % NH2P;
-                int n2 = 0;
-                while (nherm(n2) <= h2) ++n2;
-                const int r2 = h2 - nherm(n2 - 1);
-                int s2 = 0;
-                while ((s2 + 1) * (s2 + 2) / 2 <= r2) ++s2;
-                const int v2 = r2 - s2 * (s2 + 1) / 2, u2 = s2 - v2, t2 = n2 - s2;
-                const int b2 = (t2 * S + u2) * S + v2;
-                const F *f0 = Fr + cd * NH1, *f1 = Fr + NCD * NH1 + cd * NH1;
-                F z0 = F(0), z1 = F(0);
-#pragma unroll
-                for (int t1 = 0; t1 <= L1; ++t1)
-#pragma unroll
-                    for (int u1 = 0; u1 <= L1 - t1; ++u1)
-#pragma unroll
-                        for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
-                            const int off = (t1 * S + u1) * S + v1;
-                            if constexpr (FP32) {
-                                const F sh = spow[t1 + u1 + v1];
-                                z0 += f0[hidx(t1, u1, v1)] * sh * R3[b2 + off];
-                                if (lr) z1 += f1[hidx(t1, u1, v1)] * sh * R3l[b2 + off];
-                            } else {
-                                z0 += f0[hidx(t1, u1, v1)] * R3[b2 + off];
-                                if (lr) z1 += f1[hidx(t1, u1, v1)] * R3l[b2 + off];
-                            }
-                        }
-                F z = z0 + z1;
-                if constexpr (FP32) z *= spow[n2];
-                YZ[it] = (n2 & 1) ? -z : z;
-            }
-            group_sync(bar, GS);
-            // d/dC per ket component pair
-            for (int cd = lane; cd < NCD; cd += GS) {
-                const int mc = cd / ND, md = cd % ND;
-                int cx, cy, dx, dy;
-                {
-                    int c = mc, q = 0;
-                    while ((q + 1) * (q + 2) / 2 <= c) ++q;
-                    cy = q - (c - q * (q + 1) / 2);
-                    cx = LC - q;
-                    c = md;
-                    q = 0;
-                    while ((q + 1) * (q + 2) / 2 <= c) ++q;
-                    dy = q - (c - q * (q + 1) / 2);
-                    dx = LD - q;
-                }
-                const int cz = LC - cx - cy, dz = LD - dx - dy;
+            // z[cd][h2] = (-1)^|h2| s^{|h2|} sum_s sum_h1 F_s[cd][h1] s^{|h1|} R_s[h1+h2],
+            // contracted at once with dE^{cd}_{h2}/dC
+            {
                 const F zc2 = (F)(2.0 * pp.za[kp]);
-                const F *z = YZ + cd * NH2P;
                 const F *Ex = Ek, *Ey = Ek + Lay::NEK, *Ez = Ek + 2 * Lay::NEK;
-                const int nx = cx + dx, ny = cy + dy, nz = cz + dz;
-                F c0 = 0, c1 = 0, c2 = 0;
-                for (int t = 0; t <= nx + 1; ++t) {
-                    const F ex = t <= nx ? Ex[ebi(cx, dx, t, KJ, KT)] : F(0);
-                    const F dxv = zc2 * Ex[ebi(cx + 1, dx, t, KJ, KT)] - (cx > 0 ? F(cx) * Ex[ebi(cx - 1, dx, t, KJ, KT)] : F(0));
-                    for (int u = 0; u <= ny + 1; ++u) {
-                        const F ey = u <= ny ? Ey[ebi(cy, dy, u, KJ, KT)] : F(0);
-                        const F dyv = zc2 * Ey[ebi(cy + 1, dy, u, KJ, KT)] - (cy > 0 ? F(cy) * Ey[ebi(cy - 1, dy, u, KJ, KT)] : F(0));
-                        for (int v = 0; v <= nz + 1; ++v) {
-                            if (t + u + v > L2 + 1) continue;
-                            const F ez = v <= nz ? Ez[ebi(cz, dz, v, KJ, KT)] : F(0);
-                            const F dzv = zc2 * Ez[ebi(cz + 1, dz, v, KJ, KT)] - (cz > 0 ? F(cz) * Ez[ebi(cz - 1, dz, v, KJ, KT)] : F(0));
-                            const F zz = z[hidx(t, u, v)];
-                            if (u <= ny && v <= nz) c0 += dxv * ey * ez * zz;
-                            if (t <= nx && v <= nz) c1 += ex * dyv * ez * zz;
-                            if (t <= nx && u <= ny) c2 += ex * ey * dzv * zz;
-                        }
+                F c0 = F(0), c1 = F(0), c2 = F(0);
+                for (int it = lane; it < NCD * NH2P; it += GS) {
+                    const int cd = it / NH2P, h2 = it % NH2P;
+                    int n2, t2, u2, v2, cx, cy, cz, dx, dy, dz;
+                    hdecode(h2, n2, t2, u2, v2);
+                    cdecode(cd / ND, LC, cx, cy, cz);
+                    cdecode(cd % ND, LD, dx, dy, dz);
+                    const int nx = cx + dx, ny = cy + dy, nz = cz + dz;
+                    if (t2 > nx + 1 || u2 > ny + 1 || v2 > nz + 1) continue;
+                    const int b2 = (t2 * S + u2) * S + v2;
+                    const F *f0 = Fr + cd * NH1, *f1 = Fr + NCD * NH1 + cd * NH1;
+                    F z0 = F(0), z1 = F(0);
+#pragma unroll
+                    for (int t1 = 0; t1 <= L1; ++t1)
+#pragma unroll
+                        for (int u1 = 0; u1 <= L1 - t1; ++u1)
+#pragma unroll
+                            for (int v1 = 0; v1 <= L1 - t1 - u1; ++v1) {
+                                const int off = (t1 * S + u1) * S + v1;
+                                if constexpr (FP32) {
+                                    const F sh = spow[t1 + u1 + v1];
+                                    z0 += f0[hidx(t1, u1, v1)] * sh * R3[b2 + off];
+                                    if (lr) z1 += f1[hidx(t1, u1, v1)] * sh * R3l[b2 + off];
+                                } else {
+                                    z0 += f0[hidx(t1, u1, v1)] * R3[b2 + off];
+                                    if (lr) z1 += f1[hidx(t1, u1, v1)] * R3l[b2 + off];
+                                }
+                            }
+                    F z = z0 + z1;
+                    if constexpr (FP32) z *= spow[n2];
+                    if (n2 & 1) z = -z;
+                    const F ex = t2 <= nx ? Ex[ebi(cx, dx, t2, KJ, KT)] : F(0);
+                    const F ey = u2 <= ny ? Ey[ebi(cy, dy, u2, KJ, KT)] : F(0);
+                    const F ez = v2 <= nz ? Ez[ebi(cz, dz, v2, KJ, KT)] : F(0);
+                    if (u2 <= ny && v2 <= nz) {
+                        const F dxv = zc2 * Ex[ebi(cx + 1, dx, t2, KJ, KT)] -
+                                      (cx > 0 ? F(cx) * Ex[ebi(cx - 1, dx, t2, KJ, KT)] : F(0));
+                        c0 += dxv * ey * ez * z;
+                    }
+                    if (t2 <= nx && v2 <= nz) {
+                        const F dyv = zc2 * Ey[ebi(cy + 1, dy, u2, KJ, KT)] -
+                                      (cy > 0 ? F(cy) * Ey[ebi(cy - 1, dy, u2, KJ, KT)] : F(0));
+                        c1 += ex * dyv * ez * z;
+                    }
+                    if (t2 <= nx && u2 <= ny) {
+                        const F dzv = zc2 * Ez[ebi(cz + 1, dz, v2, KJ, KT)] -
+                                      (cz > 0 ? F(cz) * Ez[ebi(cz - 1, dz, v2, KJ, KT)] : F(0));
+                        c2 += ex * ey * dzv * z;
                     }
                 }
                 acc[6] += (double)c0;
@@ -507,6 +390,57 @@ __device__ void quartet_coop(F *sm, int lane, int bar, const GeoArgs &geo, const
             }
             group_sync(bar, GS);
         }
+
+        // Y[ab][h1] = sum_s sum_cd Gamma_s[ab][cd] W_s[cd][h1], contracted at once
+        // with dE^{ab}_{h1}/dA (d/dA) and with E^{ab}_{h1 - 1_x} (d/dA + d/dB)
+        {
+            const F za2 = (F)(2.0 * pp.za[ip]);
+            const F *Ex = Eb, *Ey = Eb + Lay::NEB, *Ez = Eb + 2 * Lay::NEB;
+            F a0 = F(0), a1 = F(0), a2 = F(0), q0 = F(0), q1 = F(0), q2 = F(0);
+            for (int it = lane; it < NAB * NH1P; it += GS) {
+                const int ab = it / NH1P, h1 = it % NH1P;
+                int n1, t, u, v, ax, ay, az, bx, by, bz;
+                hdecode(h1, n1, t, u, v);
+                cdecode(ab / NB, LA, ax, ay, az);
+                cdecode(ab % NB, LB, bx, by, bz);
+                const int nx = ax + bx, ny = ay + by, nz = az + bz;
+                if (t > nx + 1 || u > ny + 1 || v > nz + 1) continue;
+                const F *g0 = gam + ab * NCD, *g1 = gaml + ab * NCD;
+                F y = F(0);
+                for (int cd = 0; cd < NCD; ++cd) {
+                    y += g0[cd] * W[cd * NH1P + h1];
+                    if (lr) y += g1[cd] * W[(NCD + cd) * NH1P + h1];
+                }
+                const F ex = t <= nx ? Ex[ebi(ax, bx, t, BJ, BT)] : F(0);
+                const F ey = u <= ny ? Ey[ebi(ay, by, u, BJ, BT)] : F(0);
+                const F ez = v <= nz ? Ez[ebi(az, bz, v, BJ, BT)] : F(0);
+                if (u <= ny && v <= nz) {
+                    const F dxv = za2 * Ex[ebi(ax + 1, bx, t, BJ, BT)] -
+                                  (ax > 0 ? F(ax) * Ex[ebi(ax - 1, bx, t, BJ, BT)] : F(0));
+                    a0 += dxv * ey * ez * y;
+                    if (t >= 1 && t - 1 <= nx) q0 += Ex[ebi(ax, bx, t - 1, BJ, BT)] * ey * ez * y;
+                }
+                if (t <= nx && v <= nz) {
+                    const F dyv = za2 * Ey[ebi(ay + 1, by, u, BJ, BT)] -
+                                  (ay > 0 ? F(ay) * Ey[ebi(ay - 1, by, u, BJ, BT)] : F(0));
+                    a1 += ex * dyv * ez * y;
+                    if (u >= 1 && u - 1 <= ny) q1 += ex * Ey[ebi(ay, by, u - 1, BJ, BT)] * ez * y;
+                }
+                if (t <= nx && u <= ny) {
+                    const F dzv = za2 * Ez[ebi(az + 1, bz, v, BJ, BT)] -
+                                  (az > 0 ? F(az) * Ez[ebi(az - 1, bz, v, BJ, BT)] : F(0));
+                    a2 += ex * ey * dzv * y;
+                    if (v >= 1 && v - 1 <= nz) q2 += ex * ey * Ez[ebi(az, bz, v - 1, BJ, BT)] * y;
+                }
+            }
+            acc[0] += (double)a0;
+            acc[1] += (double)a1;
+            acc[2] += (double)a2;
+            acc[3] += (double)q0;
+            acc[4] += (double)q1;
+            acc[5] += (double)q2;
+        }
+        group_sync(bar, GS);
     }
 }
 
@@ -673,9 +607,9 @@ namespace tg {
 // classes with at least 54 function quartets and the fp32 classes with at
 // least 648, the thread kernel for every class below 648 (above, its
 // per-thread arrays run to tens of KB of local memory).  By default the
-// cooperative kernel runs for the fp64 classes from 216 function quartets
-// on ((dd|ds) and larger, measured faster there) and wherever it is the
-// only one.  ClassLaunch::kind = 1 / 2 forces the
+// cooperative kernel runs for the fp64 classes where it measured faster on
+// GB300, (dp|ds) and every class from 216 function quartets on, and wherever
+// it is the only one.  ClassLaunch::kind = 1 / 2 forces the
 // thread / cooperative kernel where both exist.
 template <int LA, int LB, int LC, int LD>
 struct UseCoop {
@@ -683,7 +617,7 @@ struct UseCoop {
     static constexpr bool fp64 = nfq >= 54;
     static constexpr bool fp32 = nfq >= 648;
     static constexpr bool thread = nfq < 648;
-    static constexpr bool fp64_default = nfq >= 216;
+    static constexpr bool fp64_default = nfq >= 216 || (LA == 2 && LB == 1 && LC == 2 && LD == 0);
 };
 
 template <int LA, int LB, int LC, int LD, typename F>
