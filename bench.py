@@ -358,7 +358,7 @@ def main():
         }
         if fp64 is not None:
             line["fp64"] = fp64
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:  # the oracle baseline is an N = 1 figure
             line["cpu_baseline"] = cpu_baseline(s, args.workload, shards=args.ref_shards)
         print(json.dumps(line))
     if dist:
