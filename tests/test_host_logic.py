@@ -1,0 +1,132 @@
+"""Host-side logic that needs no GPU: the workload generator's structure, the
+bench's class table and bookkeeping, and the router's budget calibration
+(against a fake of the library, on the CPU)."""
+import glob
+import os
+
+import numpy as np
+import pytest
+
+import bench
+from paper_2407_16586_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("index,natom,nbf,nshell,npair", [(0, 6, 50, 24, 2), (1, 32, 290, 135, 3),
+                                                         (3, 300, 2790, 1287, 3)])
+def test_workload_sizes(index, natom, nbf, nshell, npair):
+    s = synth.config(index)
+    assert (s["natom"], s["nbf"], len(s["shell_l"]), len(s["pairs"])) == (natom, nbf, nshell, npair)
+    assert max(s["shell_l"]) == 2
+    # basis functions counted from the shells (Cartesian: 1, 3, 6)
+    assert sum((l + 1) * (l + 2) // 2 for l in s["shell_l"]) == nbf
+
+
+def test_workloads_are_seeded():
+    a, b = synth.config(1), synth.config(1)
+    assert np.array_equal(a["xyz"], b["xyz"]) and np.array_equal(a["exps"], b["exps"])
+    for (A1, B1, *c1), (A2, B2, *c2) in zip(a["pairs"], b["pairs"]):
+        assert np.array_equal(A1, A2) and np.array_equal(B1, B2) and c1 == c2
+
+
+def test_c2_pairs_follow_the_reading():
+    """[(P,P), (P_delta,P), (X,X)], c_J = 1, c_K = 0.157706, c_K_lr = 1, omega = 0.3;
+    P symmetric positive semidefinite of rank 5, X normalised to |X|_F = 1."""
+    s = synth.config(1)
+    (P, P2, *c0), (Pd, P3, *c1), (X, X2, *c2) = s["pairs"]
+    assert P is P2 or np.array_equal(P, P2)
+    assert np.array_equal(P3, P)
+    assert np.array_equal(X, X2)
+    for c in (c0, c1, c2):
+        assert c == [1.0, 0.157706, 1.0, 0.3]
+    assert np.allclose(P, P.T)
+    w = np.linalg.eigvalsh(P)
+    assert w.min() > -1e-10 and np.sum(w > 1e-8 * w.max()) == 5
+    assert abs(np.linalg.norm(X) - 1.0) < 1e-12
+
+
+def test_c3_batch_sizes():
+    mols = synth.config(2)
+    assert len(mols) == 64
+    assert all(20 <= m["natom"] <= 120 for m in mols)
+
+
+def test_class_table_matches_the_kernels():
+    """bench.class_ls() index = the library's class index = the class file number."""
+    names = "spd"
+    files = sorted(os.path.basename(f) for f in glob.glob(os.path.join(ROOT, "paper_2407_16586_gb300", "csrc",
+                                                                        "class_*.cu")))
+    assert len(files) == 21
+    for qc, (la, lb, lc, ld) in enumerate(bench.class_ls()):
+        assert files[qc] == "class_%02d_%s%s%s%s.cu" % (qc, names[la], names[lb], names[lc], names[ld])
+        assert la >= lb and lc >= ld
+
+
+def test_flop_model_is_monotone_in_angular_momentum():
+    f = {c: bench.flops_per_prim_quartet(*c) for c in bench.class_ls()}
+    assert f[(0, 0, 0, 0)] == 132          # (ss|ss): 66 FMAs
+    assert f[(2, 2, 2, 2)] > f[(2, 2, 2, 1)] > f[(2, 2, 1, 1)] > f[(1, 1, 1, 1)]
+    # one operator costs less than two
+    assert bench.flops_per_prim_quartet(1, 1, 1, 1, nops=1) < f[(1, 1, 1, 1)]
+
+
+def test_workload_names():
+    s, name = bench.workload("chain:5:6:6")
+    assert s["natom"] == 12 and "6 heavy + 6 H" in name
+    assert bench.workload("c1")[0]["natom"] == 6
+    with pytest.raises(ValueError):
+        bench.workload("c9")
+
+
+def test_clock_summary():
+    rows = ["0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "1, 1000, 2070, 100.0, 0x0, Active, Not Active, Not Active, Not Active"]
+    c = bench._clocks_summary(rows, 0)
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    assert bench._clocks_summary([], 0)["sm_mhz"] is None
+
+
+class _FakeRouter:
+    def __init__(self):
+        self.calib = np.array([1.0, 1e-6, 1.0], np.float32)
+
+    def get(self):
+        return None, None, None, self.calib.copy()
+
+    def set(self, calib=None, **kw):
+        self.calib = np.asarray(calib, np.float32)
+
+
+def test_budget_calibration_keeps_the_last_safe_margin(monkeypatch):
+    """A fake library whose mixed-route error grows by 3x per 0.5 of margin
+    lowered: calibrate_budget must stop at the first margin over
+    mixed_tol / safety and keep the one before it."""
+    from paper_2407_16586_gb300 import router
+    r = _FakeRouter()
+
+    class FakeBasis:
+        def __init__(self, s):
+            pass
+
+        def grad2e(self, pairs, screen_tol=1e-10, precision=0, router=None, mixed_tol=1e-6):
+            g = np.zeros((2, 3))
+            if precision == router_mod.TG_MIXED_LEARNED:
+                m = float(router.calib[0])
+                g[0, 0] = 1e-8 * 3.0 ** ((1.0 - m) / 0.5)
+            return g, {"fp32_quartets": 1, "quartets": 2}
+
+        def close(self):
+            pass
+
+    router_mod = router.tg
+    monkeypatch.setattr(router_mod, "Basis", FakeBasis)
+    log = router.calibrate_budget(r, [{"pairs": []}], mixed_tol=1e-6, safety=5.0)
+    errs = [e for _, e, _ in log]
+    assert all(b > a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] > 2e-7 and errs[-2] <= 2e-7
+    assert float(r.calib[0]) == pytest.approx(log[-2][0])
+    assert float(r.calib[1]) == pytest.approx(1e-6)
