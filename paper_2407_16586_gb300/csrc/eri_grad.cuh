@@ -621,7 +621,7 @@ __device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const Pri
                     float a0 = 0.f, a1 = 0.f, a2 = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f;
 #pragma unroll
                     for (int t = 0; t <= L1 + 1; ++t) {
-                        float ux = 0.f, uy = 0.f, uz = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+                        float ux = 0.f, uy = 0.f, uz = 0.f, vy = 0.f, vz = 0.f;
 #pragma unroll
                         for (int u = 0; u <= L1 + 1 - t; ++u) {
                             float sE = 0.f, sD = 0.f, sS = 0.f;
