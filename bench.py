@@ -30,7 +30,6 @@ WORKLOAD = "c2: 32-atom C/N/O/H chain, 3s2p1d/2s1p Cartesian, 290 bf, 3 density 
 TAU = 1e-10
 L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
-# FLOPs per primitive quartet of the MD-GF algorithm (FMA = 2), see the design doc.
 # DRAM bytes per primitive quartet of a class kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the kernel's primitive
 # quartets) on the 12-atom chain "chain:5:6:6"; the bench scales it to the
@@ -39,6 +38,11 @@ L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 TRAFFIC_PER_PQ = {("thread", (2, 1, 1, 1), False): 10.019916e9 / 521142}
 
 
+# FLOPs per primitive quartet of the McMurchie-Davidson algorithm with the density
+# contraction folded into half-transformed Hermite vectors (FMA = 2 FLOPs): the R
+# tensors of both operators, the G rows, y = G.R, z = F.R and the derivative dot
+# products, in the thread kernel's order; the roofline uses this one count for
+# both kernel kinds.
 def _nherm(L):
     return 0 if L < 0 else (L + 1) * (L + 2) * (L + 3) // 6
 
