@@ -101,6 +101,48 @@ def test_c4_full_size_shard(tg):
     assert np.abs(g - ref).max() <= TOL
 
 
+def test_omega_infinity_is_the_full_operator(tg):
+    """erf(omega r)/r -> 1/r as omega -> inf: an lr exchange pair at omega = +inf
+    gives the full-range exchange gradient."""
+    s = synth.molecule(15, 2, 2)
+    A = s["pairs"][0][0]
+    X = s["pairs"][-1][0]
+    b = tg.Basis(s)
+    g_lr, st1 = b.grad2e([(A, X, 0.0, 0.0, 1.0, float("inf"))], screen_tol=0.0)
+    g_full, st2 = b.grad2e([(A, X, 0.0, 1.0, 0.0, 0.0)], screen_tol=0.0)
+    assert st1["quartets"] == st2["quartets"]
+    assert np.abs(g_lr - g_full).max() <= 1e-12 * max(1.0, np.abs(g_full).max())
+
+
+def test_single_atom_has_zero_gradient(tg):
+    """Every quartet of one atom is one-centre; its derivative integrals sum to
+    zero over the centres (eq. ti)."""
+    s = synth.molecule(16, 1, 0)
+    assert s["natom"] == 1
+    g, st = tg.grad2e(s, screen_tol=0.0)
+    assert st["quartets"] > 0
+    assert np.abs(g).max() <= 1e-10
+
+
+def test_eight_pairs(tg):
+    """The largest pair list (TG_MAX_PAIRS = 8), mixed coefficients and
+    operators, against the oracle."""
+    s = synth.molecule(11, 2, 3)
+    P, X = s["pairs"][0][0], s["pairs"][-1][0]
+    rng = np.random.default_rng(3)
+    mats = [P, X, X.T.copy(), P + X]
+    pairs = []
+    for k in range(8):
+        A, B = mats[k % 4], mats[(k + 1) % 4]
+        cj, ck, cl = (float(v) for v in rng.uniform(-1.0, 1.0, 3))
+        pairs.append((A, B, cj, ck, cl, 0.3))
+    b = tg.Basis(s)
+    g, st = b.grad2e(pairs, screen_tol=0.0)
+    ref, _, nq = oracle.grad2e(s, pairs=pairs, tau=0.0)
+    assert st["quartets"] == nq
+    assert np.abs(g - ref).max() <= TOL
+
+
 def test_bitwise_deterministic(tg, c1):
     g1, _ = tg.grad2e(c1, screen_tol=1e-12)
     g2, _ = tg.grad2e(c1, screen_tol=1e-12)
