@@ -757,6 +757,22 @@ MolDesc make_desc(const Plan &pl, int atom_off)
     return md;
 }
 
+// Two CUDA events for timing, destroyed on every return path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t create()
+    {
+        cudaError_t e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        return e;
+    }
+    ~EventPair()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 // Tiles of a batch per (class, precision), grouped by molecule, each
 // molecule's tiles sorted by decreasing cost.
 struct Exec {
@@ -808,11 +824,9 @@ int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, dou
     const size_t sgrad = (size_t)3 * ex.natom_max * sizeof(double);
     out.use_smem = (stage + sgrad) <= 160 * 1024;
     const size_t smem = stage + (out.use_smem ? sgrad : 0);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (timing) {
-        TG_CUDA(cudaEventCreate(&e0));
-        TG_CUDA(cudaEventCreate(&e1));
-    }
+    EventPair ev;
+    if (timing) TG_CUDA(ev.create());
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     int rc = TG_OK;
     for (int qc = 0; qc < NQC && rc == TG_OK; ++qc) {
         for (int r = 0; r < 2; ++r) {
@@ -853,10 +867,6 @@ int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, dou
                 if (stats) (r ? stats->class_ms_fp32 : stats->class_ms)[qc] += ms;
             }
         }
-    }
-    if (timing) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
     }
     return rc;
 }
@@ -1148,9 +1158,9 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
     bt->kinds.assign(2 * NQC, opt.reserved[1]);
     const int nsm = std::max(1, bt->bases[0]->nsm);
     if (opt.reserved[0] == 1) {
-        cudaEvent_t e0, e1;
-        TG_CUDA(cudaEventCreate(&e0));
-        TG_CUDA(cudaEventCreate(&e1));
+        EventPair ev;
+        TG_CUDA(ev.create());
+        cudaEvent_t e0 = ev.a, e1 = ev.b;
         for (int k = 0; k < 2 * NQC; ++k) {
             const long long nt = bt->ex.off[k + 1] - bt->ex.off[k];
             if (nt <= nsm) continue;
@@ -1168,11 +1178,7 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
                     int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt,
                                          nullptr, boys, G, gr.data(), false, st, nullptr, dummy, kd.data());
                     cudaEventRecord(e1, st);
-                    if (rc != TG_OK) {
-                        cudaEventDestroy(e0);
-                        cudaEventDestroy(e1);
-                        return rc;
-                    }
+                    if (rc != TG_OK) return rc;
                     TG_CUDA(cudaEventSynchronize(e1));
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, e0, e1);
@@ -1183,8 +1189,6 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
                     }
                 }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         bt->G = G = std::max(G, *std::max_element(bt->grids.begin(), bt->grids.end()));
     }
     // the partial slabs must cover the largest tuned grid
