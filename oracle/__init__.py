@@ -38,23 +38,27 @@ def build(force=False):
     return _LIB
 
 
+def _configure(lib):
+    """Declare the C signatures on a loaded build of tdgrad_oracle.c."""
+    lib.or_boys.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
+    lib.or_normalise.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp]
+    basis_args = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _ip, _dp, _dp]
+    lib.or_shell_eri.argtypes = basis_args + [ctypes.c_int] * 4 + [ctypes.c_double, _dp]
+    lib.or_shell_eri_deriv.argtypes = basis_args + [ctypes.c_int] * 4 + [ctypes.c_double, _dp]
+    lib.or_schwarz.argtypes = basis_args + [_dp, _dp]
+    lib.or_grad2e.argtypes = basis_args + [
+        ctypes.c_int, ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, _dp, _dp, _dp,
+        ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.or_grad2e.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        lib.or_boys.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp]
-        lib.or_normalise.argtypes = [ctypes.c_int, _ip, _ip, _dp, _dp, _dp]
-        basis_args = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _ip, _dp, _dp]
-        lib.or_shell_eri.argtypes = basis_args + [ctypes.c_int] * 4 + [ctypes.c_double, _dp]
-        lib.or_shell_eri_deriv.argtypes = basis_args + [ctypes.c_int] * 4 + [ctypes.c_double, _dp]
-        lib.or_schwarz.argtypes = basis_args + [_dp, _dp]
-        lib.or_grad2e.argtypes = basis_args + [
-            ctypes.c_int, ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, _dp, _dp, _dp,
-            ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-            ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]
-        lib.or_grad2e.restype = ctypes.c_int
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(_LIB))
     return _lib
 
 

@@ -51,6 +51,13 @@
  *      max(key(a,b), key(c,d)) mod nranks == rank,
  *      key(x,y) = X(X+1)/2 + Y with X = max(x,y), Y = min(x,y).
  */
+/* OR_MUTATION (default 0) plants one deliberate mistake for the mutation
+ * test (tests/test_oracle_mutations.py), which builds the variants into a
+ * temporary directory and checks that the pins catch each of them; the
+ * oracle itself is always built with OR_MUTATION = 0. */
+#ifndef OR_MUTATION
+#define OR_MUTATION 0
+#endif
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -114,7 +121,11 @@ static void boys_ld(int mmax, long double T, long double *F)
         }
         long double et = expl(-T);
         F[mmax] = et * sum;
+#if OR_MUTATION == 4
+        for (int m = mmax; m > 0; --m) F[m - 1] = (2.0L * T * F[m] - et) / (long double)(2 * m - 1);
+#else
         for (int m = mmax; m > 0; --m) F[m - 1] = (2.0L * T * F[m] + et) / (long double)(2 * m - 1);
+#endif
     } else {
         long double et = expl(-T);
         F[0] = 0.5L * sqrtl(3.14159265358979323846264338327950288L / T) * erfl(sqrtl(T));
@@ -174,7 +185,11 @@ void or_normalise(int nshell, const int *sh_l, const int *sh_nprim, const double
         double nk[64];
         for (int k = 0; k < K; ++k) {
             double z = exps[off + k];
+#if OR_MUTATION == 5
+            nk[k] = pow(2.0 * z / M_PI, 0.75) * pow(4.0 * z, 1.0 * l) / sqrt(df);
+#else
             nk[k] = pow(2.0 * z / M_PI, 0.75) * pow(4.0 * z, 0.5 * l) / sqrt(df);
+#endif
         }
         double s2 = 0.0;
         for (int k = 0; k < K; ++k)
@@ -244,7 +259,11 @@ static void vrr(vrr_ws *w, int Le, int Lf,
     if (omega > 0) {
         double th2 = isinf(omega) ? 1.0 : omega * omega / (omega * omega + rho);
         boys_ld(M, (long double)th2 * (long double)T, F);
+#if OR_MUTATION == 3
+        double thp = 1.0;
+#else
         double th = sqrt(th2), thp = th;
+#endif
         for (int m = 0; m <= M; ++m) { G[m] = (double)F[m] * thp; thp *= th2; }
     } else {
         boys_ld(M, (long double)T, F);
@@ -276,7 +295,11 @@ static void vrr(vrr_ws *w, int Le, int Lf,
             for (int m = 0; m <= M - tri_l[e] - tri_l[f]; ++m) {
                 double v = QC[i] * V[VIX(e, fm, m)] + WQ[i] * V[VIX(e, fm, m + 1)];
                 if (fmm >= 0) v += fmi / (2.0 * q) * (V[VIX(e, fmm, m)] - rho / q * V[VIX(e, fmm, m + 1)]);
+#if OR_MUTATION == 2
+                if (em >= 0) v -= ei / (2.0 * (p + q)) * V[VIX(em, fm, m + 1)];
+#else
                 if (em >= 0) v += ei / (2.0 * (p + q)) * V[VIX(em, fm, m + 1)];
+#endif
                 V[VIX(e, f, m)] = v;
             }
         }
@@ -299,7 +322,11 @@ static double hrr(const double *Tab, int orient, int a, int b, int c, int d, con
     int bo = orient & 1, ko = (orient >> 1) & 1;
     int e0 = bo ? b : a, x = bo ? a : b;       /* built index, expanded index */
     int f0 = ko ? d : c, y = ko ? c : d;
+#if OR_MUTATION == 9
+    double sb = bo ? 1.0 : -1.0, sk = ko ? -1.0 : 1.0;
+#else
     double sb = bo ? -1.0 : 1.0, sk = ko ? -1.0 : 1.0;   /* (B-A) = -(A-B) */
+#endif
     double R1[3] = {sb * AB[0], sb * AB[1], sb * AB[2]}, R2[3] = {sk * CD[0], sk * CD[1], sk * CD[2]};
     int ex = tri_x[e0], ey = tri_y[e0], ez = tri_z[e0];
     int xx = tri_x[x], xy = tri_y[x], xz = tri_z[x];
@@ -414,7 +441,7 @@ static double deriv_int(const quartet_ws *q, int o, int X, int i, int a, int b, 
     int tu[4] = {a, b, c, d};
     tu[X] = tshift(t[X], i, +1);
     double v = tab_int(q, o, 1 + X, tu[0], tu[1], tu[2], tu[3], AB, CD);
-    if (ni > 0) {
+    if (ni > 0 && OR_MUTATION != 1) {
         int td[4] = {a, b, c, d};
         td[X] = tshift(t[X], i, -1);
         v -= ni * tab_int(q, o, 0, td[0], td[1], td[2], td[3], AB, CD);
@@ -628,8 +655,13 @@ static void do_quartet(const obasis *bs, quartet_ws *q, const opairs *pp, int sa
                         gamma_ordered(pp, nbf, m, n, l, s, &g0, &g1);
                     } else {
                         /* the 8 images of (m n|l s) */
+#if OR_MUTATION == 6
+                        int img[8][4] = {{m, n, l, s}, {n, m, l, s}, {m, n, s, l}, {n, m, s, l},
+                                         {l, s, m, n}, {s, l, m, n}, {l, s, m, n}, {s, l, n, m}};
+#else
                         int img[8][4] = {{m, n, l, s}, {n, m, l, s}, {m, n, s, l}, {n, m, s, l},
                                          {l, s, m, n}, {s, l, m, n}, {l, s, n, m}, {s, l, n, m}};
+#endif
                         for (int t = 0; t < 8; ++t) {
                             double x0, x1;
                             gamma_ordered(pp, nbf, img[t][0], img[t][1], img[t][2], img[t][3], &x0, &x1);
@@ -653,7 +685,7 @@ static void do_quartet(const obasis *bs, quartet_ws *q, const opairs *pp, int sa
                 }
     if (want_grad)
         for (int X = 0; X < 4; ++X)
-            for (int i = 0; i < 3; ++i) grad[atoms[X] * 3 + i] += gl[X * 3 + i];
+            for (int i = 0; i < 3; ++i) grad[atoms[(OR_MUTATION == 8 && X == 2) ? 3 : X] * 3 + i] += gl[X * 3 + i];
     if (energy) *energy += el;
 }
 
@@ -828,7 +860,7 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
                         double scale = 1.0;
                         if (a == b) scale *= 0.5;
                         if (c == d) scale *= 0.5;
-                        if (ab == cd) scale *= 0.5;
+                        if (ab == cd && OR_MUTATION != 7) scale *= 0.5;
                         do_quartet(&bs, &q, &pp, a, b, c, d, 1, scale, gacc + (size_t)t * natom * 3,
                                    Ep ? Ep + t : NULL, want_grad, keep ? keep + keep_off[ab] : NULL,
                                    keep ? keep + keep_off[cd] : NULL);

@@ -95,6 +95,23 @@ def test_normalisation_unit_self_overlap(c1):
         off += K
 
 
+def test_normalisation_primitives_unit_norm(c1):
+    """Contraction coefficients multiply unit-norm primitives: c_k / d_k =
+    N_c N_k for one N_c per shell, with 1 / N_k^2 the primitive's norm."""
+    cn = oracle.normalised_coefs(c1)
+    off = 0
+    for l, K in zip(c1["shell_l"], c1["shell_nprim"]):
+        r = []
+        for k in range(K):
+            z = c1["exps"][off + k]
+            ix = integrate.quad(lambda x: x ** (2 * l) * math.exp(-2 * z * x * x), -np.inf, np.inf,
+                                epsabs=0, epsrel=1e-13)[0]
+            iy = integrate.quad(lambda x: math.exp(-2 * z * x * x), -np.inf, np.inf, epsabs=0, epsrel=1e-13)[0]
+            r.append((cn[off + k] / c1["coefs"][off + k]) ** 2 * ix * iy * iy)
+        assert max(r) - min(r) <= 1e-11 * max(r)
+        off += K
+
+
 def test_ssss_closed_form():
     rng = np.random.default_rng(5)
     for _ in range(6):

@@ -1,0 +1,173 @@
+"""The pins have teeth: each plausible mistake planted in the oracle (built
+with -DOR_MUTATION=k into a temporary directory, never shipped) must fail the
+pin named beside it, while the real oracle passes every pin.
+
+Pins used here (all independent of the oracle's own formulas):
+  boys        F_0 closed form and the defining integral by quadrature
+  norm        unit self-overlap of a normalised d shell and unit-norm
+              primitives under its coefficients, by quadrature
+  ssss        closed-form [ss|ss] of both operators (Boys F_0 only)
+  quadrature  a (pp|ps) primitive quartet of both operators against the
+              Gaussian-geminal quadrature of tests/test_oracle_integrals.py
+  fd          central finite differences of E(R) (h = 1e-4 bohr, 1e-7)
+  canonical   plain (all ordered quartets) = canonical (8 images/stabiliser)
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2407_16586_gb300 import synth
+from test_oracle_integrals import _cart, _mini_system, geminal_eri
+
+MUTATIONS = {
+    1: ("derivative rule without its lowering term", "fd"),
+    2: ("wrong sign of the electron-transfer term of the vertical recursion", "quadrature"),
+    3: ("theta^(2m) instead of theta^(2m+1) for the erf operator", "ssss"),
+    4: ("wrong sign in the downward Boys recursion", "boys"),
+    5: ("(4 zeta)^l instead of (4 zeta)^(l/2) in the primitive norm", "norm"),
+    6: ("one exchange image listed twice, another missing", "canonical"),
+    7: ("stabiliser factor of (ab) = (cd) dropped", "canonical"),
+    8: ("d/dC added to the atom of D", "fd"),
+    9: ("wrong sign of A - B in the horizontal transfer", "quadrature"),
+}
+
+
+def pin_boys():
+    for T in (0.7, 3.0, 12.0):
+        F = oracle.boys(8, T)
+        if abs(F[0] - 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))) > 1e-14:
+            return False
+        for m in (3, 8):
+            ref = integrate.quad(lambda t: t ** (2 * m) * math.exp(-T * t * t), 0.0, 1.0, epsabs=0.0,
+                                 epsrel=1e-13)[0]
+            if abs(F[m] - ref) > 1e-13 * ref:
+                return False
+    return True
+
+
+def pin_norm():
+    z = np.array([3.1, 0.9, 0.25])
+    s = dict(natom=1, xyz=np.zeros((1, 3)), shell_atom=np.zeros(1, np.int32), shell_l=np.array([2], np.int32),
+             shell_nprim=np.array([3], np.int32), exps=z, coefs=np.array([0.3, 0.6, 0.4]))
+    c = oracle.normalised_coefs(s)
+    tot = 0.0
+    for k in range(3):
+        for j in range(3):
+            zz = z[k] + z[j]
+            ix = integrate.quad(lambda x: x ** 4 * math.exp(-zz * x * x), -np.inf, np.inf, epsabs=0, epsrel=1e-13)[0]
+            iy = integrate.quad(lambda x: math.exp(-zz * x * x), -np.inf, np.inf, epsabs=0, epsrel=1e-13)[0]
+            tot += c[k] * c[j] * ix * iy * iy
+    if abs(tot - 1.0) > 1e-11:
+        return False
+    # the coefficients multiply unit-norm primitives: c_k / d_k = N_c N_k with
+    # 1 / N_k^2 the primitive's own norm, so c_k^2 / d_k^2 * norm_k is one constant
+    d = s["coefs"]
+    r = []
+    for k in range(3):
+        ix = integrate.quad(lambda x: x ** 4 * math.exp(-2 * z[k] * x * x), -np.inf, np.inf, epsabs=0, epsrel=1e-13)[0]
+        iy = integrate.quad(lambda x: math.exp(-2 * z[k] * x * x), -np.inf, np.inf, epsabs=0, epsrel=1e-13)[0]
+        r.append((c[k] / d[k]) ** 2 * ix * iy * iy)
+    return max(r) - min(r) <= 1e-11 * max(r)
+
+
+def pin_ssss():
+    cen = np.array([[0.0, 0.1, 0.2], [0.9, -0.3, 0.4], [-0.5, 1.1, 0.0], [0.3, 0.8, -0.9]])
+    z = np.array([1.3, 0.4, 2.2, 0.7])
+    s = _mini_system([0, 0, 0, 0], cen, z)
+    c = oracle.normalised_coefs(s)
+    p, q = z[0] + z[1], z[2] + z[3]
+    P = (z[0] * cen[0] + z[1] * cen[1]) / p
+    Q = (z[2] * cen[2] + z[3] * cen[3]) / q
+    kab = math.exp(-z[0] * z[1] / p * np.sum((cen[0] - cen[1]) ** 2))
+    kcd = math.exp(-z[2] * z[3] / q * np.sum((cen[2] - cen[3]) ** 2))
+    rho = p * q / (p + q)
+    T = rho * np.sum((P - Q) ** 2)
+    for w in (0.0, 0.3):
+        th2 = 1.0 if w == 0 else w * w / (w * w + rho)
+        Tw = T * th2
+        f0 = 0.5 * math.sqrt(math.pi / Tw) * math.erf(math.sqrt(Tw))
+        ref = np.prod(c) * 2 * math.pi ** 2.5 / (p * q * math.sqrt(p + q)) * kab * kcd * math.sqrt(th2) * f0
+        if abs(oracle.shell_eri(s, 0, 1, 2, 3, omega=w)[0, 0, 0, 0] - ref) > 1e-13 * abs(ref):
+            return False
+    return True
+
+
+def pin_quadrature():
+    ls = (1, 1, 1, 0)
+    cen = np.array([[0.0, 0.2, -0.1], [1.1, -0.4, 0.3], [-0.6, 0.9, 0.5], [0.4, -1.0, 0.8]])
+    z = np.array([0.8, 1.9, 0.6, 1.2])
+    s = _mini_system(list(ls), cen, z)
+    c = np.prod(oracle.normalised_coefs(s))
+    comps = [_cart(l) for l in ls]
+    for w in (0.0, 0.3):
+        got = oracle.shell_eri(s, 0, 1, 2, 3, omega=w)
+        for ii in [(0, 0, 0, 0), (1, 2, 0, 0), (2, 1, 1, 0), (0, 2, 2, 0)]:
+            prims = [(comps[k][ii[k]], cen[k], z[k]) for k in range(4)]
+            ref = c * geminal_eri(prims, 0.0, math.inf if w == 0 else w)
+            if abs(got[ii] - ref) > 1e-11 * np.abs(got).max():
+                return False
+    return True
+
+
+def _small():
+    return synth.molecule(21, 1, 2)
+
+
+def pin_fd():
+    s = _small()
+    g, _, _ = oracle.grad2e(s)
+    h = 1e-4
+    for atom, i in [(0, 0), (1, 1), (2, 2)]:
+        xp = s["xyz"].copy()
+        xp[atom, i] += h
+        xm = s["xyz"].copy()
+        xm[atom, i] -= h
+        ep = oracle.grad2e(s, xyz=xp, want_grad=False, want_energy=True)[1]
+        em = oracle.grad2e(s, xyz=xm, want_grad=False, want_energy=True)[1]
+        if abs((ep - em) / (2 * h) - g[atom, i]) > 1e-7:
+            return False
+    return True
+
+
+def pin_canonical():
+    s = _small()
+    a, x = s["pairs"][0][0], s["pairs"][-1][0]
+    pairs = [(a, x, 0.7, 0.4, 0.9, 0.3)]
+    gp, _, _ = oracle.grad2e(s, pairs=pairs, mode="plain")
+    gc, _, _ = oracle.grad2e(s, pairs=pairs, mode="canonical")
+    return np.abs(gp - gc).max() <= 1e-12 * max(1.0, np.abs(gp).max())
+
+
+PINS = {"boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
+        "canonical": pin_canonical}
+
+
+def test_real_oracle_passes_every_pin():
+    for name, pin in PINS.items():
+        assert pin(), name
+
+
+@pytest.fixture(scope="module")
+def variants(tmp_path_factory):
+    d = tmp_path_factory.mktemp("oracle_mutants")
+    src = os.path.join(os.path.dirname(oracle.__file__), "tdgrad_oracle.c")
+    out = {}
+    for k in MUTATIONS:
+        path = str(d / ("mutant%d.so" % k))
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE",
+                               "-DOR_MUTATION=%d" % k, src, "-o", path, "-lm"])
+        out[k] = path
+    return out
+
+
+@pytest.mark.parametrize("k", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(k, variants, monkeypatch):
+    what, pin = MUTATIONS[k]
+    monkeypatch.setattr(oracle, "_lib", oracle._configure(ctypes.CDLL(variants[k])))
+    assert not PINS[pin](), "mutation %d (%s) passed the %s pin" % (k, what, pin)
