@@ -129,7 +129,11 @@ static void boys_ld(int mmax, long double T, long double *F)
     } else {
         long double et = expl(-T);
         F[0] = 0.5L * sqrtl(3.14159265358979323846264338327950288L / T) * erfl(sqrtl(T));
+#if OR_MUTATION == 12
+        for (int m = 0; m < mmax; ++m) F[m + 1] = ((long double)(2 * m + 1) * F[m] + et) / (2.0L * T);
+#else
         for (int m = 0; m < mmax; ++m) F[m + 1] = ((long double)(2 * m + 1) * F[m] - et) / (2.0L * T);
+#endif
     }
 }
 
@@ -617,7 +621,11 @@ static inline void gamma_ordered(const opairs *pp, int nbf, int m, int n, int l,
     for (int p = 0; p < pp->npair; ++p) {
         const double *A = pp->A[p], *B = pp->B[p];
         double j = A[(size_t)m * nbf + n] * B[(size_t)l * nbf + s];
+#if OR_MUTATION == 10
+        double k = A[(size_t)l * nbf + m] * B[(size_t)n * nbf + s];
+#else
         double k = A[(size_t)m * nbf + l] * B[(size_t)n * nbf + s];
+#endif
         a0 += pp->cJ[p] * j + pp->cK[p] * k;
         a1 += pp->cKlr[p] * k;
     }

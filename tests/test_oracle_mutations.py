@@ -11,6 +11,8 @@ Pins used here (all independent of the oracle's own formulas):
               Gaussian-geminal quadrature of tests/test_oracle_integrals.py
   fd          central finite differences of E(R) (h = 1e-4 bohr, 1e-7)
   canonical   plain (all ordered quartets) = canonical (8 images/stabiliser)
+  gamma       the paper's Gamma (eq. gamma) written as a 4-index tensor and
+              contracted with the oracle's derivative integrals = the pair list
 """
 import ctypes
 import math
@@ -35,11 +37,13 @@ MUTATIONS = {
     7: ("stabiliser factor of (ab) = (cd) dropped", "canonical"),
     8: ("d/dC added to the atom of D", "fd"),
     9: ("wrong sign of A - B in the horizontal transfer", "quadrature"),
+    10: ("transposed first exchange density, A_lm B_ns instead of A_ml B_ns", "gamma"),
+    12: ("wrong sign in the upward Boys recursion (large T)", "boys"),
 }
 
 
 def pin_boys():
-    for T in (0.7, 3.0, 12.0):
+    for T in (0.7, 3.0, 12.0, 45.0):
         F = oracle.boys(8, T)
         if abs(F[0] - 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))) > 1e-14:
             return False
@@ -144,7 +148,39 @@ def pin_canonical():
     return np.abs(gp - gc).max() <= 1e-12 * max(1.0, np.abs(gp).max())
 
 
-PINS = {"boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
+def pin_gamma():
+    """Eq. gamma's Gamma and Gamma^lr as 4-index tensors against the pairs
+    (R,R; 2, -a, -b) + (D,P; 1/2, -a/4, -b/4), on a 2-atom s,p / s basis."""
+    s = dict(natom=2, xyz=np.array([[0.0, 0.0, 0.0], [0.4, -0.9, 1.2]]), shell_atom=np.array([0, 0, 1], np.int32),
+             shell_l=np.array([0, 1, 0], np.int32), shell_nprim=np.array([1, 1, 1], np.int32),
+             exps=np.array([1.1, 0.7, 0.5]), coefs=np.ones(3))
+    nbf, off = 5, [0, 1, 4, 5]
+    rng = np.random.default_rng(11)
+    Cm = rng.normal(0, 0.3, size=(nbf, 2))
+    P = Cm @ Cm.T
+    Pd = 0.3 * P + rng.normal(0, 0.05, size=(nbf, nbf))
+    Pd = Pd + Pd.T
+    R = rng.normal(size=(nbf, nbf)) / nbf
+    D = P + 2 * Pd
+    al, be, w = 0.157706, 1 - 0.157706, 0.3
+    G = (2 * np.einsum("nm,ls->mnls", R, R) - al * np.einsum("sm,ln->mnls", R, R)
+         + 0.5 * (np.einsum("mn,ls->mnls", D, P) - al / 2 * np.einsum("ms,ln->mnls", D, P)))
+    Glr = -be * np.einsum("sm,ln->mnls", R, R) - be / 4 * np.einsum("ms,ln->mnls", D, P)
+    g = np.zeros((2, 3))
+    for a in range(3):
+        for b in range(3):
+            for c in range(3):
+                for d in range(3):
+                    sl = tuple(slice(off[x], off[x + 1]) for x in (a, b, c, d))
+                    gg = (np.einsum("xiabcd,abcd->xi", oracle.shell_eri_deriv(s, a, b, c, d), G[sl]) +
+                          np.einsum("xiabcd,abcd->xi", oracle.shell_eri_deriv(s, a, b, c, d, omega=w), Glr[sl]))
+                    for X, sh in enumerate((a, b, c, d)):
+                        g[s["shell_atom"][sh]] += gg[X]
+    g2, _, _ = oracle.grad2e(s, pairs=[(R, R, 2.0, -al, -be, w), (D, P, 0.5, -al / 4, -be / 4, w)])
+    return np.abs(g2 - g).max() <= 1e-12 * np.abs(g).max()
+
+
+PINS = {"gamma": pin_gamma, "boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
         "canonical": pin_canonical}
 
 
