@@ -56,7 +56,9 @@ extern "C" {
 
 #define TG_OK 0
 #define TG_EINVAL (-1)        /* bad argument (null, size, exponent <= 0 ...) */
-#define TG_EUNSUPPORTED (-2)  /* l > 2, more than one lr omega, too many pairs */
+#define TG_EUNSUPPORTED (-2)  /* l > 2, more than one lr omega, too many pairs, or a size
+                                 beyond int32 indexing: nshell (nshell+1)/2 >= 2^31 shell
+                                 pairs, or >= 2^31 primitive pairs kept in one call */
 #define TG_ENOMEM (-3)        /* device or host allocation failed */
 #define TG_ECUDA (-4)         /* a CUDA runtime call failed */
 #define TG_ETIMEOUT (-5)      /* a bounded device wait expired */

@@ -221,7 +221,7 @@ const char *tg_strerror(int s)
     switch (s) {
     case TG_OK: return "ok";
     case TG_EINVAL: return "invalid argument";
-    case TG_EUNSUPPORTED: return "unsupported input (l > 2, several lr omegas, too many pairs)";
+    case TG_EUNSUPPORTED: return "unsupported input (l > 2, several lr omegas, too many pairs, size beyond int32 indexing)";
     case TG_ENOMEM: return "out of memory";
     case TG_ECUDA: return "CUDA runtime error";
     case TG_ETIMEOUT: return "bounded device wait expired";
@@ -465,6 +465,8 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
         nk_all += (long long)pl.cls[c].size();
         for (auto &hp : pl.cls[c]) npp_max += hp.np;
     }
+    // primitive-pair offsets are int32 on the device
+    if (npp_max > 0x7fffffffLL) return TG_EUNSUPPORTED;
     // ---- arena 2: pair arrays, primitive-pair records, tiles, features, partials
     pl.G = std::max(1, 4 * b->nsm);  // partial slabs: up to 4 resident CTAs per SM
     {
