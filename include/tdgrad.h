@@ -183,7 +183,8 @@ int tg_router_create(unsigned long long seed, tg_router **out);  /* Xavier-unifo
 void tg_router_destroy(tg_router *r);
 /* params: tg_router_nparam() floats (W1[32][16], b1, W2[32][32], b2, w3[32], b3);
  * mu, sd: 16 feature means / standard deviations; calib: {margin, eps_rel, trained}.
- * Any pointer may be NULL. */
+ * Any pointer may be NULL.  tg_router_set returns TG_EINVAL, changing nothing,
+ * when a value is not finite, an sd is <= 0 or eps_rel < 0. */
 int tg_router_get(const tg_router *r, float *params, float *mu, float *sd, float *calib);
 int tg_router_set(tg_router *r, const float *params, const float *mu, const float *sd, const float *calib);
 /* GPU training: standardise the features, then `epochs` full-batch Adam steps
@@ -220,6 +221,11 @@ int tg_router_predict(const tg_router *r, int n, const float *X, float *out);
  * first call before any stream capture. */
 int tg_router_loss_grad_noalloc(int n, const float *X, const float *y, const float *mu, const float *sd,
                                 const float *params, float q, float *loss, float *grad, void *stream);
+/* Router file: int32 {0x54524754 ("TGRT"), version 1, 16, 32}, then the
+ * parameters, mu, sd and {margin, eps_rel, trained} as float32, in the host's
+ * byte order.  tg_router_load returns TG_EROUTER (and *out = NULL) for a
+ * missing, short or foreign file, or one holding non-finite values or an
+ * sd <= 0. */
 int tg_router_save(const tg_router *r, const char *path);
 int tg_router_load(const char *path, tg_router **out);
 

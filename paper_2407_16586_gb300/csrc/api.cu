@@ -1353,15 +1353,21 @@ int tg_router_get(const tg_router *r, float *params, float *mu, float *sd, float
 int tg_router_set(tg_router *r, const float *params, const float *mu, const float *sd, const float *calib)
 {
     if (!r) return TG_EINVAL;
+    // validate everything first: on error the router is left as it was
+    if (params)
+        for (int k = 0; k < NPARAM; ++k)
+            if (!std::isfinite(params[k])) return TG_EINVAL;
+    if (mu)
+        for (int j = 0; j < NFEAT; ++j)
+            if (!std::isfinite(mu[j])) return TG_EINVAL;
+    if (sd)
+        for (int j = 0; j < NFEAT; ++j)
+            if (!(sd[j] > 0.f) || !std::isfinite(sd[j])) return TG_EINVAL;
+    if (calib && (!std::isfinite(calib[0]) || !(calib[1] >= 0.f) || !std::isfinite(calib[1]))) return TG_EINVAL;
     if (params) std::memcpy(r->params, params, sizeof(r->params));
     if (mu) std::memcpy(r->mu, mu, sizeof(r->mu));
-    if (sd) {
-        for (int j = 0; j < NFEAT; ++j)
-            if (!(sd[j] > 0.f)) return TG_EINVAL;
-        std::memcpy(r->sd, sd, sizeof(r->sd));
-    }
+    if (sd) std::memcpy(r->sd, sd, sizeof(r->sd));
     if (calib) {
-        if (!std::isfinite(calib[0]) || !(calib[1] >= 0.f)) return TG_EINVAL;
         r->margin = calib[0];
         r->eps_rel = calib[1];
         r->trained = calib[2] != 0.f;
@@ -1507,6 +1513,9 @@ int tg_router_load(const char *path, tg_router **out)
               std::fread(r->mu, sizeof(r->mu), 1, f) == 1 && std::fread(r->sd, sizeof(r->sd), 1, f) == 1 &&
               std::fread(cal, sizeof(cal), 1, f) == 1;
     std::fclose(f);
+    for (int k = 0; ok && k < NPARAM; ++k) ok = std::isfinite(r->params[k]);
+    for (int j = 0; ok && j < NFEAT; ++j) ok = std::isfinite(r->mu[j]) && r->sd[j] > 0.f && std::isfinite(r->sd[j]);
+    ok = ok && std::isfinite(cal[0]) && cal[1] >= 0.f && std::isfinite(cal[1]);
     if (!ok) {
         delete r;
         return TG_EROUTER;
