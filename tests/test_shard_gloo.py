@@ -67,3 +67,58 @@ def test_two_rank_shard_sum():
         assert units == float(nq_all)           # shards partition the quartets
     assert res[0][1] + res[1][1] == nq_all
     assert res[0][1] > 0 and res[1][1] > 0
+
+
+def _leaving_worker(rank, world, port, out):
+    import datetime
+    import time
+
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_2407_16586_gb300 import synth
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    s = synth.molecule(3, 1, 2)
+    g, _, _ = oracle.grad2e(s, tau=1e-12, rank=rank, nranks=world, nthreads=1)
+    if rank == 1:
+        # this rank fails between steps: it leaves without joining the sum
+        out[rank] = "left"
+        os._exit(3)
+    t0 = time.time()
+    try:
+        dist.all_reduce(torch.from_numpy(g.copy()))
+        out[rank] = "completed"
+    except Exception as e:  # the survivor's collective ends with an error
+        out[rank] = ("error", type(e).__name__, time.time() - t0)
+    os._exit(0)
+
+
+def test_rank_that_leaves_ends_the_others_sum_with_an_error():
+    """Failure detection on the host: a rank that exits between steps never
+    joins the gradient sum; the surviving rank's all-reduce ends with an
+    error within the process group's timeout instead of hanging."""
+    import oracle
+
+    oracle.build()
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        procs = [ctx.Process(target=_leaving_worker, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+        for p in procs:
+            if p.is_alive():
+                p.kill()
+        res = dict(out)
+        codes = [p.exitcode for p in procs]
+    assert res.get(1) == "left" and codes[1] == 3
+    assert codes[0] == 0
+    assert isinstance(res.get(0), tuple) and res[0][0] == "error", res.get(0)
+    assert res[0][2] < 60.0
