@@ -74,6 +74,17 @@ def flops_per_prim_quartet(la, lb, lc, ld, nops=2):
     return 2 * fma
 
 
+def print_opcount():
+    """The FLOP model per angular class: function quartets and FLOPs per
+    primitive quartet (both operators), one row per class."""
+    names = "spd"
+    nc = lambda l: (l + 1) * (l + 2) // 2
+    print("%-3s %-8s %6s %12s" % ("#", "class", "nfq", "flop/pq"))
+    for qc, (la, lb, lc, ld) in enumerate(class_ls()):
+        print("%-3d %-8s %6d %12d" % (qc, "(%s%s|%s%s)" % (names[la], names[lb], names[lc], names[ld]),
+                                      nc(la) * nc(lb) * nc(lc) * nc(ld), flops_per_prim_quartet(la, lb, lc, ld)))
+
+
 def _clock_sampler(stop, rows):
     cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -212,7 +223,11 @@ def main():
     ap.add_argument("--ref-shards", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", help='c2 (default), c1, or chain:SEED:NHEAVY:NH')
+    ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
     args = ap.parse_args()
+    if args.opcount:
+        print_opcount()
+        return 0
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
