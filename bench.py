@@ -194,6 +194,51 @@ def run_reference(args):
     return 0
 
 
+# Derived ALU peaks (TFLOP/s) of GB300: 152 SMs x (2 fp64 | 128 fp32) FMA per
+# clock per SM x 2 FLOP x 2.07 GHz.
+PEAK_TFLOPS = {"fp64": 152 * 2 * 2 * 2.07e9 / 1e12, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
+
+
+def default_kernel_is_coop(la, lb, lc, ld, fp32):
+    """The library's per-class default kernel kind: a thread group per
+    quartet from 648 function quartets in fp32, from 216 (and for (dp|ds)) in
+    fp64; one quartet per thread otherwise."""
+    nc = lambda l: (l + 1) * (l + 2) // 2
+    nfq = nc(la) * nc(lb) * nc(lc) * nc(ld)
+    return nfq >= 648 if fp32 else (nfq >= 216 or (la, lb, lc, ld) == (2, 1, 2, 0))
+
+
+def roofline_entry(st_t):
+    """Roofline of the dominant class kernel of one timed call (stats with
+    per-class CUDA-event times): its algorithmic FLOPs over its time against
+    the derived ALU peak of its precision, and its DRAM traffic per launch
+    where a capture of that kernel exists."""
+    names = "spd"
+    best = None
+    for qc in range(21):
+        for fp32 in (False, True):
+            ms = (st_t["class_ms_fp32"] if fp32 else st_t["class_ms"])[qc]
+            if ms > 0 and (best is None or ms > best[0]):
+                best = (ms, qc, fp32)
+    ms, qc, fp32 = best
+    npq, flops = _flops_of(st_t, qc, fp32)
+    la, lb, lc, ld = class_ls()[qc]
+    achieved = flops / (ms / 1e3) / 1e12
+    pk = PEAK_TFLOPS["fp32" if fp32 else "fp64"]
+    coop = default_kernel_is_coop(la, lb, lc, ld, fp32)
+    kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if coop else "", names[la], names[lb], names[lc], names[ld],
+                                           "fp32" if fp32 else "fp64")
+    key = ("coop" if coop else "thread", (la, lb, lc, ld), fp32)
+    tot_flops = sum(_flops_of(st_t, q, f)[1] for q in range(21) for f in (False, True))
+    tot_ms = sum(st_t["class_ms"]) + sum(st_t["class_ms_fp32"])
+    return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk,
+            "traffic": TRAFFIC_PER_PQ[key] * npq if key in TRAFFIC_PER_PQ else None,
+            "peak_source": "derived: 152 SM x (2 fp64 | 128 fp32) FMA/clk x 2 flop x 2.07 GHz",
+            "kernel_ms": ms, "kernel_prim_quartets": npq,
+            "all_kernels_tflops": tot_flops / (tot_ms / 1e3) / 1e12 if tot_ms > 0 else None}
+
+
 def cpu_baseline(s, name, shards=600, shard=0):
     import oracle
     oracle.build()
@@ -330,28 +375,6 @@ def main():
                 "speedup_vs_fp64": (ms64 / args.fp64_steps) / (t_max / args.steps)}
 
     if rank == 0:
-        peaks = {"fp64": 152 * 2 * 2 * 2.07e9 / 1e12, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
-        names = "spd"
-        best = None
-        for qc in range(21):
-            for fp32 in (False, True):
-                ms = (st_t["class_ms_fp32"] if fp32 else st_t["class_ms"])[qc]
-                if ms > 0 and (best is None or ms > best[0]):
-                    best = (ms, qc, fp32)
-        ms, qc, fp32 = best
-        npq, flops = _flops_of(st_t, qc, fp32)
-        la, lb, lc, ld = class_ls()[qc]
-        achieved = flops / (ms / 1e3) / 1e12
-        pk = peaks["fp32" if fp32 else "fp64"]
-        nc = lambda l: (l + 1) * (l + 2) // 2
-        nfq = nc(la) * nc(lb) * nc(lc) * nc(ld)
-        # the library's default kernel per class
-        coop = nfq >= 648 if fp32 else (nfq >= 216 or (la, lb, lc, ld) == (2, 1, 2, 0))
-        kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if coop else "",
-                                               names[la], names[lb], names[lc], names[ld],
-                                               "fp32" if fp32 else "fp64")
-        tot_flops = sum(_flops_of(st_t, q, f)[1] for q in range(21) for f in (False, True))
-        tot_ms = sum(st_t["class_ms"]) + sum(st_t["class_ms_fp32"])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -365,14 +388,7 @@ def main():
             "e2e": {"value": e2e_q / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                         "frac": achieved / pk,
-                         "traffic": (TRAFFIC_PER_PQ[("coop" if coop else "thread", (la, lb, lc, ld), fp32)] * npq
-                                     if ("coop" if coop else "thread", (la, lb, lc, ld), fp32) in TRAFFIC_PER_PQ
-                                     else None),
-                         "peak_source": "derived: 152 SM x (2 fp64 | 128 fp32) FMA/clk x 2 flop x 2.07 GHz",
-                         "kernel_ms": ms, "kernel_prim_quartets": npq,
-                         "all_kernels_tflops": tot_flops / (tot_ms / 1e3) / 1e12 if tot_ms > 0 else None},
+            "roofline": roofline_entry(st_t),
             "clocks": _clocks_summary(rows, local),
         }
         if fp64 is not None:

@@ -130,3 +130,55 @@ def test_budget_calibration_keeps_the_last_safe_margin(monkeypatch):
     assert errs[-1] > 2e-7 and errs[-2] <= 2e-7
     assert float(r.calib[0]) == pytest.approx(log[-2][0])
     assert float(r.calib[1]) == pytest.approx(1e-6)
+
+
+def _fake_stats(ms64, ms32, pq64, pq32):
+    z = [0.0] * 21
+    st = {"class_ms": list(z), "class_ms_fp32": list(z), "class_prim_quartets": [0] * 21,
+          "class_prim_quartets_fp32": [0] * 21}
+    for qc, v in ms64.items():
+        st["class_ms"][qc] = v
+    for qc, v in ms32.items():
+        st["class_ms_fp32"][qc] = v
+    for qc, v in pq64.items():
+        st["class_prim_quartets"][qc] = v
+    for qc, v in pq32.items():
+        st["class_prim_quartets_fp32"][qc] = v
+    return st
+
+
+def test_roofline_of_the_dominant_kernel():
+    """achieved = algorithmic FLOPs of the longest class launch / its time;
+    frac against the derived fp64 (or fp32) ALU peak; traffic scaled from the
+    captured bytes per primitive quartet where that kernel was captured."""
+    ls = bench.class_ls()
+    dppp, dddd = ls.index((2, 1, 1, 1)), ls.index((2, 2, 2, 2))
+    st = _fake_stats({dppp: 600.0, 0: 5.0}, {dddd: 100.0}, {dppp: 4_850_000, 0: 10_000}, {dddd: 20_000})
+    r = bench.roofline_entry(st)
+    flops = 4_850_000 * bench.flops_per_prim_quartet(2, 1, 1, 1)
+    assert r["kernel"] == "k_grad<(dp|pp), fp64>"
+    assert r["achieved"] == pytest.approx(flops / 0.6 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] == pytest.approx(10.019916e9 / 521142 * 4_850_000)
+    tot = flops + 10_000 * bench.flops_per_prim_quartet(0, 0, 0, 0) + 20_000 * bench.flops_per_prim_quartet(2, 2, 2, 2)
+    assert r["all_kernels_tflops"] == pytest.approx(tot / 0.705 / 1e12)
+    # an fp32 cooperative launch that dominates: its own peak, no captured traffic
+    st = _fake_stats({dppp: 50.0}, {dddd: 100.0}, {dppp: 1000}, {dddd: 20_000})
+    r = bench.roofline_entry(st)
+    assert r["kernel"] == "k_grad_coop<(dd|dd), fp32>"
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert r["traffic"] is None
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+
+
+def test_default_kernel_kind_follows_the_class_split():
+    assert not bench.default_kernel_is_coop(2, 1, 1, 1, False)        # (dp|pp), 162 function quartets
+    assert bench.default_kernel_is_coop(2, 1, 2, 0, False)            # (dp|ds) defaults to the group kernel
+    assert bench.default_kernel_is_coop(2, 2, 2, 0, False)            # (dd|ds), 216
+    assert not bench.default_kernel_is_coop(2, 2, 2, 0, True)         # fp32 from 648
+    assert bench.default_kernel_is_coop(2, 2, 2, 1, True)             # (dd|dp), 648
+    # the same split as the library's compile-time choice
+    src = open(os.path.join(ROOT, "paper_2407_16586_gb300", "csrc", "eri_coop.cuh")).read()
+    assert "fp32 = nfq >= 648" in src
+    assert "fp64_default = nfq >= 216 || (LA == 2 && LB == 1 && LC == 2 && LD == 0)" in src
