@@ -270,6 +270,25 @@ class Basis:
         return g, st.as_dict()
 
 
+def tda_pairs(P, P_delta, R, alpha, beta, omega):
+    """The density pairs of the TDA excited-state gradient's two-electron
+    term (Sec. II.A, eq. gamma): Gamma holds 2 R R (Coulomb-like), -alpha R R
+    and -beta R R through the full and erf(omega r)/r operators (exchange-
+    like), and the ground-state and relaxed-difference densities through
+    D = P + 2 P_delta paired with P, with a factor 1/2 and exchange weights
+    -alpha/4, -beta/4.  P is the ground-state density, P_delta the relaxed
+    difference density and R the transition density (X in the AO basis),
+    each nbf x nbf row-major, numpy arrays or torch CUDA tensors.
+
+    Pairs are bilinear in their first matrix, so (D, P) is passed as
+    (P, P) + 2 (P_delta, P): the list holds three pairs and the helper does no
+    arithmetic on the matrices."""
+    a, b = float(alpha), float(beta)
+    return [(R, R, 2.0, -a, -b, omega),
+            (P, P, 0.5, -a / 4.0, -b / 4.0, omega),
+            (P_delta, P, 1.0, -a / 2.0, -b / 2.0, omega)]
+
+
 def grad2e(system, pairs=None, **kw):
     """One-shot gradient of a dict-shaped system (builds and frees a Basis)."""
     b = Basis(system)

@@ -149,6 +149,11 @@ def test_gamma_mapping_matches_paper_gamma():
     pairs = [(R, R, 2.0, -al, -be, w), (D, P, 0.5, -al / 4, -be / 4, w)]
     g2, _, _ = oracle.grad2e(s, pairs=pairs)
     np.testing.assert_allclose(g2, g, atol=1e-12 * np.abs(g).max(), rtol=0)
+    # the binding's helper passes the same Gamma as three pairs, (D, P) split
+    # into (P, P) + 2 (P_delta, P)
+    from paper_2407_16586_gb300 import tda_pairs
+    g3, _, _ = oracle.grad2e(s, pairs=tda_pairs(P, Pd, R, al, be, w))
+    np.testing.assert_allclose(g3, g, atol=1e-12 * np.abs(g).max(), rtol=0)
 
 
 def test_plain_equals_canonical(small):
