@@ -409,8 +409,16 @@ static void contract_tables(const obasis *bs, quartet_ws *q, int sa, int sb, int
                     if (keep_cd && !keep_cd[kc * bs->sh_nprim[sd] + kd]) continue;
                     double za = bs->exps[bs->sh_off[sa] + ka], zb = bs->exps[bs->sh_off[sb] + kb];
                     double zc = bs->exps[bs->sh_off[sc] + kc], zd = bs->exps[bs->sh_off[sd] + kd];
+#if OR_MUTATION == 13
+                    double cc = bs->cn[bs->sh_off[sa] + ka] * bs->cn[bs->sh_off[sb] + kb] *
+                                bs->cn[bs->sh_off[sc] + kc] * bs->cn[bs->sh_off[sd] + kc % bs->sh_nprim[sd]];
+#elif OR_MUTATION == 14
+                    double cc = bs->cn[bs->sh_off[sa] + ka] * bs->cn[bs->sh_off[sb]] *
+                                bs->cn[bs->sh_off[sc] + kc] * bs->cn[bs->sh_off[sd] + kd];
+#else
                     double cc = bs->cn[bs->sh_off[sa] + ka] * bs->cn[bs->sh_off[sb] + kb] *
                                 bs->cn[bs->sh_off[sc] + kc] * bs->cn[bs->sh_off[sd] + kd];
+#endif
                     double wts[5] = {cc, cc * 2 * za, cc * 2 * zb, cc * 2 * zc, cc * 2 * zd};
                     int bo = zb > za, ko = zd > zc, r = bo | (ko << 1);
                     for (int o = 0; o < nops; ++o) {

@@ -13,6 +13,9 @@ Pins used here (all independent of the oracle's own formulas):
   canonical   plain (all ordered quartets) = canonical (8 images/stabiliser)
   gamma       the paper's Gamma (eq. gamma) written as a 4-index tensor and
               contracted with the oracle's derivative integrals = the pair list
+  contraction a (pp|ps) quartet of 2-3-primitive shells of both operators
+              against the quadrature of tests/test_oracle_contraction.py, with
+              that file's own normalisation
 """
 import ctypes
 import math
@@ -26,6 +29,7 @@ from scipy import integrate
 import oracle
 from paper_2407_16586_gb300 import synth
 from test_oracle_integrals import _cart, _mini_system, geminal_eri
+from test_oracle_contraction import contracted_reference, oracle_system, random_shells
 
 MUTATIONS = {
     1: ("derivative rule without its lowering term", "fd"),
@@ -39,6 +43,8 @@ MUTATIONS = {
     9: ("wrong sign of A - B in the horizontal transfer", "quadrature"),
     10: ("transposed first exchange density, A_lm B_ns instead of A_ml B_ns", "gamma"),
     12: ("wrong sign in the upward Boys recursion (large T)", "boys"),
+    13: ("coefficient of shell d taken at shell c's primitive index", "contraction"),
+    14: ("first primitive's coefficient of shell b used for all its primitives", "contraction"),
 }
 
 
@@ -180,7 +186,18 @@ def pin_gamma():
     return np.abs(g2 - g).max() <= 1e-12 * np.abs(g).max()
 
 
-PINS = {"gamma": pin_gamma, "boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
+def pin_contraction():
+    shells = random_shells((1, 1, 1, 0), (2, 3, 2, 2), seed=77)
+    s = oracle_system(shells)
+    for w in (0.0, 0.3):
+        ref = contracted_reference(shells, w)
+        got = oracle.shell_eri(s, 0, 1, 2, 3, omega=w)
+        if np.abs(got - ref).max() > 1e-11 * np.abs(ref).max():
+            return False
+    return True
+
+
+PINS = {"gamma": pin_gamma, "contraction": pin_contraction, "boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
         "canonical": pin_canonical}
 
 
