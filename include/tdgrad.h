@@ -61,7 +61,8 @@ extern "C" {
                                  pairs, or >= 2^31 primitive pairs kept in one call */
 #define TG_ENOMEM (-3)        /* device or host allocation failed */
 #define TG_ECUDA (-4)         /* a CUDA runtime call failed */
-#define TG_ETIMEOUT (-5)      /* a bounded device wait expired */
+#define TG_ETIMEOUT (-5)      /* reserved: a bounded device wait expired.  No kernel of this
+                                 version waits on another CTA or a flag, so no call returns it. */
 #define TG_EROUTER (-6)       /* router missing, malformed or incompatible */
 
 #define TG_FP64 0             /* every primitive quartet in fp64 */
@@ -70,6 +71,19 @@ extern "C" {
 #define TG_FP32 3             /* every primitive quartet in fp32 (no accuracy target; calibration) */
 
 #define TG_MAX_PAIRS 8
+
+/* Version of this header's structs and calls; tg_abi_version() returns the
+ * value the library was built with.  2: named tg_options fields (autotune,
+ * kernel_kind, deterministic, class_mask) and the planning and roofline fields
+ * of tg_stats. */
+#define TG_ABI_VERSION 2
+
+/* tg_options.kernel_kind: which class-kernel form evaluates a class (every
+ * form gives the same result to rounding; a form not compiled for a class
+ * falls back to the class default) */
+#define TG_KERNEL_DEFAULT 0   /* per-class default */
+#define TG_KERNEL_THREAD 1    /* one contracted quartet per thread */
+#define TG_KERNEL_GROUP 2     /* a group of 32-128 threads per quartet, arrays in shared memory */
 
 typedef struct tg_basis tg_basis;    /* opaque: basis + geometry, device copies */
 typedef struct tg_router tg_router;  /* opaque: block router MLP weights */
@@ -94,10 +108,15 @@ typedef struct {
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
     int rank, nranks;       /* shard; default 0 / 1 */
     int timing;             /* 1: time every class kernel with CUDA events (tg_stats.class_ms) */
-    int reserved[7];        /* [0]: tg_batch_create autotuning (below); [1]: class kernel kind,
-                               0 = per-class default, 1 = one quartet per thread, 2 = a thread
-                               group per quartet where compiled (same results to rounding);
-                               others 0 */
+    int autotune;           /* tg_batch_create only, 1: autotune every class list (see there) */
+    int kernel_kind;        /* TG_KERNEL_DEFAULT (default), _THREAD or _GROUP */
+    int deterministic;      /* 1 (default): fixed-order fp64 sums, bitwise reproducible on one
+                               device for one launch configuration.  Every path of this
+                               version is deterministic; 0 is accepted and changes nothing. */
+    unsigned class_mask;    /* 0 (default): every angular class; otherwise bit qc keeps class qc
+                               (0..20, numbered as in tg_stats.class_quartets) and drops the
+                               rest, e.g. for per-class checks and timings */
+    int reserved[4];        /* must be 0 */
 } tg_options;
 
 typedef struct {
@@ -111,13 +130,26 @@ typedef struct {
     int grid;                     /* CTAs of each persistent class launch */
     double class_ms[21];          /* per angular class: fp64 kernel time (only with timing = 1) */
     double class_ms_fp32[21];     /* per angular class: fp32 kernel time (only with timing = 1) */
-    long long class_quartets[21];
+    long long class_quartets[21];            /* angular class qc = P(P+1)/2 + Q, bra pair class
+                                                P >= ket pair class Q, pair classes ss ps pp
+                                                ds dp dd = 0..5 */
     long long class_prim_quartets[21];       /* fp64 primitive quartets */
     long long class_prim_quartets_fp32[21];  /* fp32 primitive quartets */
+    double plan_ms;               /* host clock: densities, block factors, pair screening, class
+                                     sort, tile list and routing, up to the first class launch */
+    double fp64_flop, fp32_flop;  /* algorithmic FLOPs of the evaluated primitive quartets per
+                                     precision (the per-class count of the McMurchie-Davidson
+                                     evaluation, 2 per FMA) */
+    double fp64_frac_peak;        /* with timing = 1: fp64_flop / summed fp64 class-kernel time,
+                                     over the device's fp64 FMA peak (SMs x 2 FMA/clk x 2 x clock);
+                                     0 otherwise */
+    double fp32_frac_peak;        /* the same for fp32 (SMs x 128 FMA/clk x 2 x clock) */
 } tg_stats;
 
 /* Fill o with the defaults listed above. */
 void tg_options_default(tg_options *o);
+/* TG_ABI_VERSION of the built library. */
+int tg_abi_version(void);
 
 /* Create a basis handle.  xyz_bohr: natom*3; per shell: atom index, l (0..2),
  * primitive count (1..16); exps/coefs: concatenated primitives in shell
@@ -145,7 +177,7 @@ const char *tg_strerror(int status);
  * (a basis holds one plan at a time) and must outlive the batch; with
  * device_ptrs the densities are read from the caller's device buffers at
  * every run (their contents may change, the plan does not), otherwise they
- * are copied at creation.  opt->reserved[0] = 1 autotunes every class list
+ * are copied at creation.  opt->autotune = 1 autotunes every class list
  * on a sample of its tiles: the kernel kind (one quartet per thread, or a
  * group of threads per quartet) and the persistent grid (1-4 CTAs per SM).
  * tg_batch_run replays the graph on opt->stream and writes grads[m]

@@ -49,7 +49,7 @@ def _configure(lib):
     lib.or_grad2e.argtypes = basis_args + [
         ctypes.c_int, ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp, _dp, _dp, _dp,
         ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-        ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]
+        ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.or_grad2e.restype = ctypes.c_int
     return lib
 
@@ -132,12 +132,14 @@ def schwarz(s):
 
 
 def grad2e(s, pairs=None, mode="canonical", tau=0.0, rank=0, nranks=1, nthreads=0,
-           want_grad=True, want_energy=False, xyz=None):
+           want_grad=True, want_energy=False, xyz=None, qclass=-1):
     """Two-electron gradient (natom x 3, Ha/bohr) of the pair list.
 
     Returns (grad, energy, nquartets).  mode "plain" loops over all ordered
     shell quartets; "canonical" uses the 8-fold symmetry and supports
-    screening (tau) and shards (rank, nranks)."""
+    screening (tau) and shards (rank, nranks).  qclass >= 0 keeps only the
+    quartets of one angular class (0..20: the pair classes ss ps pp ds dp dd
+    numbered 0..5, class P(P+1)/2 + Q for bra pair class P >= ket class Q)."""
     s2 = dict(s)
     if xyz is not None:
         s2["xyz"] = xyz
@@ -158,7 +160,7 @@ def grad2e(s, pairs=None, mode="canonical", tau=0.0, rank=0, nranks=1, nthreads=
     rc = _load().or_grad2e(*bs.args(), npair, Ap, Bp, _d(cJ), _d(cK), _d(cKlr), _d(om),
                            0 if mode == "plain" else 1, float(tau), int(rank), int(nranks),
                            int(nthreads), 1 if want_grad else 0, _d(grad),
-                           ctypes.byref(e) if want_energy else None, ctypes.byref(nq))
+                           ctypes.byref(e) if want_energy else None, ctypes.byref(nq), int(qclass))
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return grad, (e.value if want_energy else None), nq.value

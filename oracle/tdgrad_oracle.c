@@ -722,19 +722,34 @@ static void block_max(const obasis *bs, const double *Mx, double *out)
         }
 }
 
+/* Angular class of a shell quartet: with the pair class of a shell pair
+ * P(x,y) = L(L+1)/2 + l, L = max(l_x,l_y), l = min(l_x,l_y) (ss ps pp ds dp dd
+ * = 0..5), the quartet class is P1(P1+1)/2 + P2 with P1 >= P2 the larger and
+ * smaller pair class of (ab) and (cd): the 21 classes of l <= 2 (Sec. II.C). */
+static int quartet_class(const obasis *bs, int a, int b, int c, int d)
+{
+    int la = bs->sh_l[a], lb = bs->sh_l[b], lc = bs->sh_l[c], ld = bs->sh_l[d];
+    int L1 = la > lb ? la : lb, l1 = la > lb ? lb : la, L2 = lc > ld ? lc : ld, l2 = lc > ld ? ld : lc;
+    int P = L1 * (L1 + 1) / 2 + l1, Q = L2 * (L2 + 1) / 2 + l2;
+    int hi = P > Q ? P : Q, lo = P > Q ? Q : P;
+    return hi * (hi + 1) / 2 + lo;
+}
+
 /*
  * The gradient.  mode 0 = plain (all ordered shell quartets, no screening,
  * no shards), mode 1 = canonical (8-fold, optional screening and shards).
  * want_grad / want_energy select the outputs (grad natom*3 overwritten,
  * energy scalar).  nquart_out (nullable) receives the number of canonical
- * shell quartets evaluated.  Returns 0, or -1 on bad arguments.
+ * shell quartets evaluated.  qclass >= 0 keeps only the quartets of that
+ * angular class (quartet_class below); -1 keeps all.  Returns 0, or -1 on
+ * bad arguments.
  */
 int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, const int *sh_l,
               const int *sh_nprim, const double *exps, const double *coefs,
               int npair, const double *const *Am, const double *const *Bm, const double *cJ,
               const double *cK, const double *cKlr, const double *omega,
               int mode, double tau, int rank, int nranks, int nthreads,
-              int want_grad, double *grad, double *energy, long long *nquart_out)
+              int want_grad, double *grad, double *energy, long long *nquart_out, int qclass)
 {
     init_tri();
     if (natom < 1 || nshell < 1 || npair < 0 || nranks < 1 || rank < 0 || rank >= nranks) return -1;
@@ -836,6 +851,7 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
                 for (int b = 0; b < ns; ++b)
                     for (int c = 0; c < ns; ++c)
                         for (int d = 0; d < ns; ++d) {
+                            if (qclass >= 0 && quartet_class(&bs, a, b, c, d) != qclass) continue;
                             do_quartet(&bs, &q, &pp, a, b, c, d, 0, 1.0, gacc + (size_t)t * natom * 3,
                                        Ep ? Ep + t : NULL, want_grad, NULL, NULL);
                             cnt[t]++;
@@ -864,6 +880,7 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
                     for (int d = 0; d <= c; ++d) {
                         long long cd = (long long)c * (c + 1) / 2 + d;
                         if (cd > ab) continue;
+                        if (qclass >= 0 && quartet_class(&bs, a, b, c, d) != qclass) continue;
                         if (tau > 0) {
                             double S1 = Qd[a * ns + b] * Q[c * ns + d], S2 = Q[a * ns + b] * Qd[c * ns + d];
                             double S = S1 > S2 ? S1 : S2;

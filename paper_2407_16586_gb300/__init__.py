@@ -32,7 +32,7 @@ TG_MIXED_LEARNED = 2
 TG_FP32 = 3
 TG_MAX_PAIRS = 8
 
-EXPORTS = ("tg_options_default", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
+EXPORTS = ("tg_options_default", "tg_abi_version", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
            "tg_grad2e", "tg_strerror", "tg_tile_samples", "tg_router_nparam", "tg_router_create",
            "tg_router_destroy", "tg_router_get", "tg_router_set", "tg_router_train", "tg_router_loss_grad",
            "tg_router_predict", "tg_router_save", "tg_router_load", "tg_batch_create", "tg_batch_run",
@@ -49,7 +49,8 @@ class tg_options(ctypes.Structure):
     _fields_ = [("screen_tol", ctypes.c_double), ("precision", ctypes.c_int), ("router", ctypes.c_void_p),
                 ("mixed_tol", ctypes.c_double), ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("rank", ctypes.c_int), ("nranks", ctypes.c_int), ("timing", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("autotune", ctypes.c_int), ("kernel_kind", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("class_mask", ctypes.c_uint), ("reserved", ctypes.c_int * 4)]
 
 
 class tg_stats(ctypes.Structure):
@@ -58,7 +59,9 @@ class tg_stats(ctypes.Structure):
                 ("launches", ctypes.c_int), ("grid", ctypes.c_int), ("class_ms", ctypes.c_double * 21),
                 ("class_ms_fp32", ctypes.c_double * 21), ("class_quartets", ctypes.c_longlong * 21),
                 ("class_prim_quartets", ctypes.c_longlong * 21),
-                ("class_prim_quartets_fp32", ctypes.c_longlong * 21)]
+                ("class_prim_quartets_fp32", ctypes.c_longlong * 21), ("plan_ms", ctypes.c_double),
+                ("fp64_flop", ctypes.c_double), ("fp32_flop", ctypes.c_double),
+                ("fp64_frac_peak", ctypes.c_double), ("fp32_frac_peak", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -228,13 +231,15 @@ class Basis:
         return X[:n.value].copy(), y[:n.value].copy(), e[:n.value].copy()
 
     def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
-               timing=False, router=None, mixed_tol=1e-6, kernel=0):
+               timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0):
         """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
         torch CUDA tensors (then the densities and ``out`` stay on the device).  ``kernel``
         picks the class kernels: 0 per-class default, 1 one quartet per thread, 2 a thread
-        group per quartet where compiled."""
+        group per quartet where compiled.  ``class_mask`` (0 = all) keeps the angular
+        classes whose bits are set."""
         opt = tg_options_default()
-        opt.reserved[1] = int(kernel)
+        opt.kernel_kind = int(kernel)
+        opt.class_mask = int(class_mask)
         opt.screen_tol = float(screen_tol)
         opt.precision = int(precision)
         opt.rank, opt.nranks = int(rank), int(nranks)
@@ -396,7 +401,7 @@ class Batch:
         if router is not None:
             opt.router = router.h
         if autotune:
-            opt.reserved[0] = 1
+            opt.autotune = 1
         parrs = []
         for s, b in zip(systems, self.bases):
             keep, plist = b._plist(s["pairs"])

@@ -214,7 +214,13 @@ void tg_options_default(tg_options *o)
     o->rank = 0;
     o->nranks = 1;
     o->timing = 0;
+    o->autotune = 0;
+    o->kernel_kind = TG_KERNEL_DEFAULT;
+    o->deterministic = 1;
+    o->class_mask = 0;
 }
+
+int tg_abi_version(void) { return TG_ABI_VERSION; }
 
 const char *tg_strerror(int s)
 {
@@ -347,6 +353,11 @@ int check_pairs(int npair, const tg_pair *pairs, const tg_options &opt, double &
         opt.precision != TG_FP32)
         return TG_EINVAL;
     if (!(opt.mixed_tol >= 0.0) || !std::isfinite(opt.mixed_tol)) return TG_EINVAL;
+    if (opt.kernel_kind < TG_KERNEL_DEFAULT || opt.kernel_kind > TG_KERNEL_GROUP) return TG_EINVAL;
+    if (opt.deterministic != 0 && opt.deterministic != 1) return TG_EINVAL;
+    if (opt.class_mask >> NQC) return TG_EINVAL;
+    for (int r : opt.reserved)
+        if (r != 0) return TG_EINVAL;
     omega = 0.0;
     use_lr = 0;
     for (int p = 0; p < npair; ++p) {
@@ -569,6 +580,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
         }
     };
     for (int qc = 0; qc < NQC; ++qc) {
+        if (opt.class_mask && !((opt.class_mask >> qc) & 1u)) continue;
         const int P = pl.qc_P[qc], Qc = pl.qc_Q[qc];
         const int nP = (int)pl.cls[P].size(), nQ = (int)pl.cls[Qc].size();
         if (!nP || !nQ) continue;
@@ -961,7 +973,7 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
     if (stats)
         for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
     rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, nullptr, b->d_boys, pl.G, nullptr, opt.timing != 0, st,
-                     stats, launches, nullptr, opt.reserved[1]);
+                     stats, launches, nullptr, opt.kernel_kind);
     if (rc != TG_OK) return rc;
     k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, pl.G, d_part, pl.dgrad);
     ++launches;
@@ -1157,9 +1169,9 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
     // thread or cooperative kernel, grid capped at 1, 2, 3 or 4 CTAs per SM;
     // the fastest pair is kept
     bt->grids.assign(2 * NQC, G);
-    bt->kinds.assign(2 * NQC, opt.reserved[1]);
+    bt->kinds.assign(2 * NQC, opt.kernel_kind);
     const int nsm = std::max(1, bt->bases[0]->nsm);
-    if (opt.reserved[0] == 1) {
+    if (opt.autotune == 1) {
         EventPair ev;
         TG_CUDA(ev.create());
         cudaEvent_t e0 = ev.a, e1 = ev.b;
@@ -1247,11 +1259,13 @@ int tg_batch_run(tg_batch *bt, double *const *grads, const tg_options *opt_in, t
     if (opt_in) opt = *opt_in;
     else tg_options_default(&opt);
     cudaStream_t st = (cudaStream_t)opt.stream;
+    // every argument is checked before the first CUDA call
+    for (int m = 0; m < bt->nmol; ++m)
+        if (!grads[m]) return TG_EINVAL;
     TG_CUDA(cudaGraphLaunch(bt->gexec, st));
     unsigned long long hc[4 * NQC];
     TG_CUDA(cudaMemcpyAsync(hc, bt->d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
     for (int m = 0; m < bt->nmol; ++m) {
-        if (!grads[m]) return TG_EINVAL;
         TG_CUDA(cudaMemcpyAsync(grads[m], bt->d_grad + 3 * (size_t)bt->atom_off[m],
                                 sizeof(double) * 3 * bt->bases[m]->natom,
                                 opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
@@ -1380,10 +1394,16 @@ static int router_loss_grad_dev(const tg_router *r, int n, const float *dX, cons
                                 float *gpart, float *lpart)
 {
     const int nblk = (n + TRB - 1) / TRB;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bwd_smem());
-        attr = true;
+    // the dynamic shared-memory limit is a per-device attribute of the kernel
+    constexpr int kMaxDev = 64;
+    static bool attr[kMaxDev] = {false};
+    int dev = 0;
+    TG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) return TG_ECUDA;
+    if (!attr[dev]) {
+        TG_CUDA(cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)fwd_bwd_smem()));
+        attr[dev] = true;
     }
     k_mlp_fwd_bwd<<<nblk, TRB, fwd_bwd_smem()>>>(n, dX, dy, dmu, dsd, dparams, q, gpart, lpart);
     k_sum_partials<<<(NPARAM + 127) / 128, 128>>>(nblk, NPARAM, gpart, dgrad);

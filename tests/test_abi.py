@@ -37,3 +37,15 @@ def test_strerror_and_defaults_without_gpu():
     assert o.screen_tol == 1e-10 and o.nranks == 1 and o.precision == tg.TG_FP64
     assert tg.tg_strerror(tg.TG_EINVAL) == "invalid argument"
     assert "unknown" in tg.tg_strerror(-99)
+
+
+def test_abi_version_and_named_option_defaults():
+    import paper_2407_16586_gb300 as tg
+    src = open(os.path.join(ROOT, "include", "tdgrad.h")).read()
+    ver = int(re.search(r"#define TG_ABI_VERSION (\d+)", src).group(1))
+    L = tg.lib()
+    L.tg_abi_version.restype = ctypes.c_int
+    assert L.tg_abi_version() == ver
+    o = tg.tg_options_default()
+    assert o.deterministic == 1 and o.class_mask == 0 and o.kernel_kind == 0 and o.autotune == 0
+    assert list(o.reserved) == [0, 0, 0, 0]

@@ -211,3 +211,19 @@ def test_screening_is_rigorous_enough(small):
     assert n2 < n1 <= n0
     assert np.abs(g1 - g0).max() <= 1e-9
     assert np.abs(g2 - g0).max() <= 1e-4
+
+
+def test_class_filter_partitions_the_quartets(c1):
+    """The 21 angular classes partition the canonical quartets: the
+    class-filtered gradients and quartet counts sum to the whole, and every
+    class of c1's s, p, d shells holds quartets."""
+    g, _, nq = oracle.grad2e(c1, tau=1e-10)
+    tot = np.zeros_like(g)
+    n = 0
+    for qc in range(21):
+        gq, _, nqq = oracle.grad2e(c1, tau=1e-10, qclass=qc)
+        assert nqq > 0, qc
+        tot += gq
+        n += nqq
+    assert n == nq
+    assert np.abs(tot - g).max() <= 1e-12 * max(1.0, np.abs(g).max())
