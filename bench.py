@@ -10,8 +10,11 @@ canonical shell quartets surviving screening ("deriv-quartets") per second.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
   python bench.py --impl reference ...   (the CPU oracle, timed on host cores)
 
-N > 1 runs as torchrun ranks; every rank evaluates its own full molecule
-(independent problems, weak scaling, no collective on the data path).
+N > 1 runs as torchrun ranks that share ONE gradient: every rank evaluates
+a tile-cyclic shard of every class list (TG_SHARD_TILES) and the natom x 3
+partials are summed with one NCCL all-reduce (strong scaling).
+
+  python bench.py --workload c4 ...   (the 300-atom cluster; one warm-up step)
 """
 import argparse
 import json
@@ -32,23 +35,15 @@ L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
 # DRAM bytes per primitive quartet of a class kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the kernel's primitive
-# quartets) on the 12-atom chain "chain:5:6:6"; the bench scales it to the
-# launch it times.  Keyed by (kernel kind, class, fp32); profiles/ holds the
+# quartets) on a smaller chain of the same recipe; the bench scales it to the
+# launch it times.  Keyed by (kernel form, class, fp32); profiles/ holds the
 # capture.  An entry is removed when its kernel changes.
-TRAFFIC_PER_PQ = {("thread", (2, 1, 1, 1), False): 10.019916e9 / 521142}
+TRAFFIC_PER_PQ = {}
 
-
-# FLOPs per primitive quartet of the McMurchie-Davidson algorithm with the density
-# contraction folded into half-transformed Hermite vectors (FMA = 2 FLOPs): the R
-# tensors of both operators, the G rows, y = G.R, z = F.R and the derivative dot
-# products, in the thread kernel's order; the roofline uses this one count for
-# both kernel kinds.
-def _nherm(L):
-    return 0 if L < 0 else (L + 1) * (L + 2) * (L + 3) // 6
-
-
-def _nherm4(L):
-    return (L + 1) * (L + 2) * (L + 3) * (L + 4) // 24
+CLASS_NAMES = ["(%s%s|%s%s)" % tuple("spd"[x] for x in ls) for ls in
+               [(0, 0, 0, 0), (1, 0, 0, 0), (1, 0, 1, 0), (1, 1, 0, 0), (1, 1, 1, 0), (1, 1, 1, 1), (2, 0, 0, 0),
+                (2, 0, 1, 0), (2, 0, 1, 1), (2, 0, 2, 0), (2, 1, 0, 0), (2, 1, 1, 0), (2, 1, 1, 1), (2, 1, 2, 0),
+                (2, 1, 2, 1), (2, 2, 0, 0), (2, 2, 1, 0), (2, 2, 1, 1), (2, 2, 2, 0), (2, 2, 2, 1), (2, 2, 2, 2)]]
 
 
 def class_ls():
@@ -60,29 +55,17 @@ def class_ls():
     return out
 
 
-def flops_per_prim_quartet(la, lb, lc, ld, nops=2):
-    nc = lambda l: (l + 1) * (l + 2) // 2
-    nab, ncd = nc(la) * nc(lb), nc(lc) * nc(ld)
-    L1, L2 = la + lb, lc + ld
-    L = L1 + L2
-    fma = 0
-    fma += nops * 2 * _nherm4(L + 1)                       # R tensors
-    fma += nops * nab * ncd * _nherm(L2)                   # G rows (Gamma . E_ket)
-    fma += nops * nab * _nherm(L2) * _nherm(L1 + 1)        # y = G . R
-    fma += nops * ncd * _nherm(L1) * _nherm(L2 + 1)        # z = F . R
-    fma += 4 * nab * _nherm(L1 + 1) + 3 * ncd * _nherm(L2 + 1)  # derivative dot products
-    return 2 * fma
-
-
 def print_opcount():
-    """The FLOP model per angular class: function quartets and FLOPs per
-    primitive quartet (both operators), one row per class."""
-    names = "spd"
+    """The library's algorithmic FLOP count per angular class (tg_class_flops):
+    per primitive quartet and per bra primitive pair, both operators."""
+    import paper_2407_16586_gb300 as tg
+    from paper_2407_16586_gb300 import build
+    build.build()
     nc = lambda l: (l + 1) * (l + 2) // 2
-    print("%-3s %-8s %6s %12s" % ("#", "class", "nfq", "flop/pq"))
+    print("%-3s %-8s %6s %12s %12s" % ("#", "class", "nfq", "flop/pq", "flop/bra-p"))
     for qc, (la, lb, lc, ld) in enumerate(class_ls()):
-        print("%-3d %-8s %6d %12d" % (qc, "(%s%s|%s%s)" % (names[la], names[lb], names[lc], names[ld]),
-                                      nc(la) * nc(lb) * nc(lc) * nc(ld), flops_per_prim_quartet(la, lb, lc, ld)))
+        a, b = tg.tg_class_flops(qc, 2)
+        print("%-3d %-8s %6d %12d %12d" % (qc, CLASS_NAMES[qc], nc(la) * nc(lb) * nc(lc) * nc(ld), a, b))
 
 
 def _clock_sampler(stop, rows):
@@ -148,13 +131,17 @@ def aggregate_over_ranks(dist, ms, units, device):
 
 def workload(name):
     """The timed system: "c2" (the default, the 32-atom chain), "c1" (6 atoms),
-    or "chain:SEED:NHEAVY:NH" (a smaller chain of the same recipe, used for
+    "c4" (the 300-atom core + water cluster, 2790 basis functions), or
+    "chain:SEED:NHEAVY:NH" (a smaller chain of the same recipe, used for
     profiler captures)."""
     from paper_2407_16586_gb300 import synth
     if name == "c1":
         return synth.config(0), "c1: 2 O + 4 H, 50 bf, 2 density pairs"
     if name == "c2":
         return synth.config(1), WORKLOAD
+    if name == "c4":
+        return synth.config(3), ("c4: 300-atom core + water cluster, 2790 bf, 3 density pairs, wB97X-like, "
+                                 "tau=1e-10")
     parts = name.split(":")
     if len(parts) == 4 and parts[0] == "chain":
         seed, nheavy, nh = (int(x) for x in parts[1:])
@@ -195,25 +182,27 @@ def run_reference(args):
 
 
 # Derived ALU peaks (TFLOP/s) of GB300: 152 SMs x (2 fp64 | 128 fp32) FMA per
-# clock per SM x 2 FLOP x 2.07 GHz.
+# clock per SM x 2 FLOP x 2.07 GHz.  MEASURED_PEAKS.json holds only the HBM
+# copy and bf16 GEMM rates, neither of which bounds this path.
 PEAK_TFLOPS = {"fp64": 152 * 2 * 2 * 2.07e9 / 1e12, "fp32": 152 * 128 * 2 * 2.07e9 / 1e12}
 
 
-def default_kernel_is_coop(la, lb, lc, ld, fp32):
-    """The library's per-class default kernel kind: a thread group per
-    quartet from 648 function quartets in fp32, from 216 (and for (dp|ds)) in
-    fp64; one quartet per thread otherwise."""
-    nc = lambda l: (l + 1) * (l + 2) // 2
-    nfq = nc(la) * nc(lb) * nc(lc) * nc(ld)
-    return nfq >= 648 if fp32 else (nfq >= 216 or (la, lb, lc, ld) == (2, 1, 2, 0))
+def class_flops(st, qc, fp32, nops=2):
+    """Algorithmic FLOPs of one class launch from the call's counters and the
+    library's per-class count (tg_class_flops)."""
+    import paper_2407_16586_gb300 as tg
+    fpq, fp = tg.tg_class_flops(qc, nops)
+    npq = (st["class_prim_quartets_fp32"] if fp32 else st["class_prim_quartets"])[qc]
+    nbv = (st["class_bra_prims_fp32"] if fp32 else st["class_bra_prims"])[qc]
+    return npq, npq * fpq + nbv * fp
 
 
-def roofline_entry(st_t):
-    """Roofline of the dominant class kernel of one timed call (stats with
-    per-class CUDA-event times): its algorithmic FLOPs over its time against
-    the derived ALU peak of its precision, and its DRAM traffic per launch
-    where a capture of that kernel exists."""
-    names = "spd"
+def roofline_entry(st_t, nops=2):
+    """Roofline of one timed call (stats with per-class CUDA-event times): the
+    dominant class kernel's algorithmic FLOPs over its time against the
+    derived ALU peak of its precision, its DRAM traffic per launch where a
+    capture of that kernel exists, and the time-weighted bound of all class
+    launches, sum(flops_64 / peak_64 + flops_32 / peak_32) / sum(time)."""
     best = None
     for qc in range(21):
         for fp32 in (False, True):
@@ -221,22 +210,34 @@ def roofline_entry(st_t):
             if ms > 0 and (best is None or ms > best[0]):
                 best = (ms, qc, fp32)
     ms, qc, fp32 = best
-    npq, flops = _flops_of(st_t, qc, fp32)
-    la, lb, lc, ld = class_ls()[qc]
+    npq, flops = class_flops(st_t, qc, fp32, nops)
     achieved = flops / (ms / 1e3) / 1e12
     pk = PEAK_TFLOPS["fp32" if fp32 else "fp64"]
-    coop = default_kernel_is_coop(la, lb, lc, ld, fp32)
-    kname = "k_grad%s<(%s%s|%s%s), %s>" % ("_coop" if coop else "", names[la], names[lb], names[lc], names[ld],
-                                           "fp32" if fp32 else "fp64")
-    key = ("coop" if coop else "thread", (la, lb, lc, ld), fp32)
-    tot_flops = sum(_flops_of(st_t, q, f)[1] for q in range(21) for f in (False, True))
-    tot_ms = sum(st_t["class_ms"]) + sum(st_t["class_ms_fp32"])
+    kname = "%s %s" % (CLASS_NAMES[qc], "fp32" if fp32 else "fp64")
+    key = (qc, fp32)
+    t_ideal, t_all, f64, f32, ms64, ms32 = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0
+    for q in range(21):
+        for f in (False, True):
+            m = (st_t["class_ms_fp32"] if f else st_t["class_ms"])[q]
+            if m <= 0:
+                continue
+            fl = class_flops(st_t, q, f, nops)[1]
+            t_ideal += fl / (PEAK_TFLOPS["fp32" if f else "fp64"] * 1e12)
+            t_all += m / 1e3
+            if f:
+                f32, ms32 = f32 + fl, ms32 + m
+            else:
+                f64, ms64 = f64 + fl, ms64 + m
     return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
             "frac": achieved / pk,
             "traffic": TRAFFIC_PER_PQ[key] * npq if key in TRAFFIC_PER_PQ else None,
             "peak_source": "derived: 152 SM x (2 fp64 | 128 fp32) FMA/clk x 2 flop x 2.07 GHz",
+            "flop_model": "tg_class_flops: McMurchie-Davidson with index boxes, per primitive quartet and bra primitive",
             "kernel_ms": ms, "kernel_prim_quartets": npq,
-            "all_kernels_tflops": tot_flops / (tot_ms / 1e3) / 1e12 if tot_ms > 0 else None}
+            "frac_mixed": t_ideal / t_all if t_all > 0 else None,
+            "fp64_frac": (f64 / (ms64 / 1e3) / 1e12 / PEAK_TFLOPS["fp64"]) if ms64 > 0 else None,
+            "fp32_frac": (f32 / (ms32 / 1e3) / 1e12 / PEAK_TFLOPS["fp32"]) if ms32 > 0 else None,
+            "class_kernels_ms": t_all * 1e3}
 
 
 def cpu_baseline(s, name, shards=600, shard=0):
@@ -250,12 +251,6 @@ def cpu_baseline(s, name, shards=600, shard=0):
             "sample": "shard %d of %d of the %s quartets (%d quartets, %.1f s)" % (shard, shards, name, nq, dt)}
 
 
-def _flops_of(st, qc, fp32):
-    la, lb, lc, ld = class_ls()[qc]
-    npq = (st["class_prim_quartets_fp32"] if fp32 else st["class_prim_quartets"])[qc]
-    return npq, npq * flops_per_prim_quartet(la, lb, lc, ld)
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,15 +260,19 @@ def main():
     ap.add_argument("--precision", default="mixed-learned", choices=["mixed-learned", "mixed-bound", "fp64", "fp32"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed fp64 steps for the comparison (0: skip)")
     ap.add_argument("--router", default=os.path.join(ROOT, "paper_2407_16586_gb300", "data", "router.bin"))
-    ap.add_argument("--ref-shards", type=int, default=600)
+    ap.add_argument("--ref-shards", type=int, default=None, help="oracle shards (default 600; 50000 for c4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", help='c2 (default), c1, or chain:SEED:NHEAVY:NH')
+    ap.add_argument("--workload", default="c2", help='c2 (default), c1, c4, or chain:SEED:NHEAVY:NH')
+    ap.add_argument("--bound-steps", type=int, default=1, help="timed mixed-bound steps for the comparison (0: skip)")
     ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
     args = ap.parse_args()
     if args.opcount:
         print_opcount()
         return 0
-    args.warmup = max(args.warmup, 3)
+    # c4 steps take minutes each: one warm-up step (the default c2 line keeps >= 3)
+    args.warmup = max(args.warmup, 1 if args.workload == "c4" else 3)
+    if args.ref_shards is None:
+        args.ref_shards = 50000 if args.workload == "c4" else 600
     if args.impl == "reference":
         return run_reference(args)
 
@@ -308,8 +307,15 @@ def main():
     gout = torch.empty((s["natom"], 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # N > 1: the ranks share ONE gradient, each taking its tile-cyclic shard of every
+    # class list, and the natom x 3 partials are summed with one NCCL all-reduce
+    shard = dict(rank=rank, nranks=world, shard_mode=tg.TG_SHARD_TILES) if world > 1 else {}
+
     def step(precision, timing=False):
-        _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=timing)
+        _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=timing,
+                             **shard)
+        if dist:
+            dist.all_reduce(gout)
         return st
 
     def timed(precision, n):
@@ -357,7 +363,11 @@ def main():
         torch.cuda.synchronize(dev)
         t = time.perf_counter()
         _, st = basis.grad2e(hpairs, screen_tol=TAU, precision=prec, router=router, out=hout,
-                             stream=stream.cuda_stream)
+                             stream=stream.cuda_stream, **shard)
+        if dist:
+            hg = torch.from_numpy(hout).to(dev)
+            dist.all_reduce(hg)
+            hout[:] = hg.cpu().numpy()
         e2e_ms += 1e3 * (time.perf_counter() - t)
         e2e_q += st["quartets"]
     e2e_ms, e2e_q = aggregate_over_ranks(dist, e2e_ms, e2e_q, dev)
@@ -373,22 +383,33 @@ def main():
         fp64 = {"ms_per_step": ms64 / args.fp64_steps, "value": q64 / (ms64 / 1e3),
                 "max_abs_dg_vs_fp64": float(np.abs(g_head - g64).max()),
                 "speedup_vs_fp64": (ms64 / args.fp64_steps) / (t_max / args.steps)}
+        # the rigorous-bound router on the same workload (same clocks)
+        if args.bound_steps > 0 and prec == tg.TG_MIXED_LEARNED:
+            stb = step(tg.TG_MIXED_BOUND)
+            gb = gout.cpu().numpy().copy()
+            msb, qb, _, _ = timed(tg.TG_MIXED_BOUND, args.bound_steps)
+            fp64["mixed_bound"] = {"ms_per_step": msb / args.bound_steps, "value": qb / (msb / 1e3),
+                                   "fp32_quartets_per_step": stb["fp32_quartets"],
+                                   "max_abs_dg_vs_fp64": float(np.abs(gb - g64).max())}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64",
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64",
             "data": "synthetic",
             "config": {"workload": wname, "precision": args.precision, "screen_tol": TAU, "mixed_tol": 1e-6,
                        "quartets_per_step": st0["quartets"], "fp32_quartets_per_step": st0["fp32_quartets"],
                        "prim_quartets_per_step": st0["prim_quartets"], "pairs": st0["pairs"], "tiles": st0["tiles"],
                        "l2": "flushed (512 MB write) before each timed step",
-                       "parallelism": "independent molecule per rank" if world > 1 else "single GPU"},
+                       "parallelism": ("one gradient, tile-cyclic shards per rank, NCCL all-reduce of natom x 3"
+                                       if world > 1 else "single GPU")},
             "e2e": {"value": e2e_q / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": roofline_entry(st_t),
+            "plan_ms": st_t["plan_ms"],
             "clocks": _clocks_summary(rows, local),
         }
         if fp64 is not None:

@@ -59,7 +59,9 @@ extern "C" {
 #define TG_EUNSUPPORTED (-2)  /* l > 2, more than one lr omega, too many pairs, or a size
                                  beyond int32 indexing: nshell (nshell+1)/2 >= 2^31 shell
                                  pairs, or >= 2^31 primitive pairs kept in one call */
-#define TG_ENOMEM (-3)        /* device or host allocation failed */
+#define TG_ENOMEM (-3)        /* device or host allocation failed (for tests: while the environment
+                                 variable TDGRAD_FAIL_ALLOC=1 is set, every growth of the library's
+                                 device work areas fails this way, without a CUDA call) */
 #define TG_ECUDA (-4)         /* a CUDA runtime call failed */
 #define TG_ETIMEOUT (-5)      /* reserved: a bounded device wait expired.  No kernel of this
                                  version waits on another CTA or a flag, so no call returns it. */
@@ -84,6 +86,7 @@ extern "C" {
 #define TG_KERNEL_DEFAULT 0   /* per-class default */
 #define TG_KERNEL_THREAD 1    /* one contracted quartet per thread */
 #define TG_KERNEL_GROUP 2     /* a group of 32-128 threads per quartet, arrays in shared memory */
+#define TG_KERNEL_WARP 3      /* one warp per quartet, every phase spread over its 32 lanes */
 
 typedef struct tg_basis tg_basis;    /* opaque: basis + geometry, device copies */
 typedef struct tg_router tg_router;  /* opaque: block router MLP weights */
@@ -109,15 +112,29 @@ typedef struct {
     int rank, nranks;       /* shard; default 0 / 1 */
     int timing;             /* 1: time every class kernel with CUDA events (tg_stats.class_ms) */
     int autotune;           /* tg_batch_create only, 1: autotune every class list (see there) */
-    int kernel_kind;        /* TG_KERNEL_DEFAULT (default), _THREAD or _GROUP */
+    int kernel_kind;        /* TG_KERNEL_DEFAULT (default), _THREAD, _GROUP or _WARP */
     int deterministic;      /* 1 (default): fixed-order fp64 sums, bitwise reproducible on one
                                device for one launch configuration.  Every path of this
                                version is deterministic; 0 is accepted and changes nothing. */
     unsigned class_mask;    /* 0 (default): every angular class; otherwise bit qc keeps class qc
                                (0..20, numbered as in tg_stats.class_quartets) and drops the
                                rest, e.g. for per-class checks and timings */
-    int reserved[4];        /* must be 0 */
+    int shard_mode;         /* TG_SHARD_PAIR_KEY (default) or TG_SHARD_TILES, see below */
+    int reserved[3];        /* must be 0 */
 } tg_options;
+
+/* tg_options.shard_mode with nranks > 1:
+ * TG_SHARD_PAIR_KEY: the quartet shards of the top of this file (pair keys mod nranks).
+ * TG_SHARD_TILES: every (class, precision) launch list, ordered by decreasing cost, is
+ *   dealt cyclically: its tile i belongs to rank i mod nranks.  Each rank then runs 1/nranks
+ *   of every class's tiles (balanced cost, no quartet filter inside the kernels); the
+ *   partial gradients of all ranks sum to the full one.  tg_grad2e only. */
+#define TG_SHARD_PAIR_KEY 0
+#define TG_SHARD_TILES 1
+
+/* The tiles of one launch list of ntiles tiles that rank evaluates under
+ * TG_SHARD_TILES: *count tiles, first, first + stride, ...  Host only. */
+int tg_tile_shard(long long ntiles, int rank, int nranks, long long *first, long long *count, long long *stride);
 
 typedef struct {
     double seconds;               /* wall time of the call (host clock) */
@@ -135,6 +152,9 @@ typedef struct {
                                                 ds dp dd = 0..5 */
     long long class_prim_quartets[21];       /* fp64 primitive quartets */
     long long class_prim_quartets_fp32[21];  /* fp32 primitive quartets */
+    long long class_bra_prims[21];           /* fp64: bra primitive pairs visited (one per
+                                                quartet and bra primitive pair) */
+    long long class_bra_prims_fp32[21];      /* the same for fp32 */
     double plan_ms;               /* host clock: densities, block factors, pair screening, class
                                      sort, tile list and routing, up to the first class launch */
     double fp64_flop, fp32_flop;  /* algorithmic FLOPs of the evaluated primitive quartets per
@@ -150,6 +170,15 @@ typedef struct {
 void tg_options_default(tg_options *o);
 /* TG_ABI_VERSION of the built library. */
 int tg_abi_version(void);
+/* Algorithmic FLOPs of angular class qc (0..20) with nops operators (1: 1/r
+ * only, 2: 1/r and erf(omega r)/r) used by tg_stats: per primitive quartet
+ * and per bra primitive pair of a quartet.  The count is that of the
+ * McMurchie-Davidson evaluation with the density contraction folded into
+ * half-transformed Hermite vectors (Sec. II.C, eqs. cartG, deriv, ti): Boys
+ * orders, the Hermite R recursion, and each contraction over the index box
+ * t <= a_x+b_x, u <= a_y+b_y, v <= a_z+b_z where a function pair's expansion
+ * coefficients can be non-zero; an FMA counts 2.  Host only, no device. */
+int tg_class_flops(int qc, int nops, double *per_prim_quartet, double *per_bra_prim);
 
 /* Create a basis handle.  xyz_bohr: natom*3; per shell: atom index, l (0..2),
  * primitive count (1..16); exps/coefs: concatenated primitives in shell
@@ -195,9 +224,12 @@ void tg_batch_destroy(tg_batch *batch);
  * extents, smallest exponent sums, primitive-pair counts) to the log10 of the
  * tile's largest contribution to one gradient component.  Mixed modes route
  * tiles to fp32 in increasing order of their error estimate e_t while
- * sum e_t^2 <= (mixed_tol/3)^2 (independent rounding errors add in
- * quadrature; 3 is the safety factor): e_t = eps_rel * 10^(prediction +
- * margin) for TG_MIXED_LEARNED, 3e-6 * 128 * nfq * bound for TG_MIXED_BOUND.
+ * sum e_t^2 <= mixed_tol^2 (independent rounding errors add in quadrature;
+ * tg_grad2e takes the tiles bin by bin, 8 bins per factor of 2 in e_t, each
+ * tile counted at its bin's upper edge): e_t = eps_rel * 10^(prediction +
+ * margin) for TG_MIXED_LEARNED, whose margin is calibrated on measured
+ * errors against the fp64 path, and 3e-6 * 128 * nfq * bound for
+ * TG_MIXED_BOUND.
  * The paper has no counterpart: its kernels are fp64 throughout (Sec. II.C,
  * II.E). */
 

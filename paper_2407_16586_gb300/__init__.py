@@ -31,8 +31,10 @@ TG_MIXED_BOUND = 1
 TG_MIXED_LEARNED = 2
 TG_FP32 = 3
 TG_MAX_PAIRS = 8
+TG_SHARD_PAIR_KEY = 0
+TG_SHARD_TILES = 1
 
-EXPORTS = ("tg_options_default", "tg_abi_version", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
+EXPORTS = ("tg_options_default", "tg_abi_version", "tg_class_flops", "tg_tile_shard", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
            "tg_grad2e", "tg_strerror", "tg_tile_samples", "tg_router_nparam", "tg_router_create",
            "tg_router_destroy", "tg_router_get", "tg_router_set", "tg_router_train", "tg_router_loss_grad",
            "tg_router_predict", "tg_router_save", "tg_router_load", "tg_batch_create", "tg_batch_run",
@@ -50,7 +52,7 @@ class tg_options(ctypes.Structure):
                 ("mixed_tol", ctypes.c_double), ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("rank", ctypes.c_int), ("nranks", ctypes.c_int), ("timing", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("kernel_kind", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("class_mask", ctypes.c_uint), ("reserved", ctypes.c_int * 4)]
+                ("class_mask", ctypes.c_uint), ("shard_mode", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class tg_stats(ctypes.Structure):
@@ -59,7 +61,8 @@ class tg_stats(ctypes.Structure):
                 ("launches", ctypes.c_int), ("grid", ctypes.c_int), ("class_ms", ctypes.c_double * 21),
                 ("class_ms_fp32", ctypes.c_double * 21), ("class_quartets", ctypes.c_longlong * 21),
                 ("class_prim_quartets", ctypes.c_longlong * 21),
-                ("class_prim_quartets_fp32", ctypes.c_longlong * 21), ("plan_ms", ctypes.c_double),
+                ("class_prim_quartets_fp32", ctypes.c_longlong * 21), ("class_bra_prims", ctypes.c_longlong * 21),
+                ("class_bra_prims_fp32", ctypes.c_longlong * 21), ("plan_ms", ctypes.c_double),
                 ("fp64_flop", ctypes.c_double), ("fp32_flop", ctypes.c_double),
                 ("fp64_frac_peak", ctypes.c_double), ("fp32_frac_peak", ctypes.c_double)]
 
@@ -129,6 +132,35 @@ def lib():
             getattr(L, n).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def tg_class_flops(qc, nops=2):
+    """(FLOPs per primitive quartet, FLOPs per bra primitive pair) of angular
+    class qc in the library's algorithmic count."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    L = lib()
+    L.tg_class_flops.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    L.tg_class_flops.restype = ctypes.c_int
+    rc = L.tg_class_flops(int(qc), int(nops), ctypes.byref(a), ctypes.byref(b))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_class_flops")
+    return a.value, b.value
+
+
+def tg_tile_shard(ntiles, rank, nranks):
+    """(first, count, stride) of the tiles of a list of ntiles that rank
+    evaluates under TG_SHARD_TILES."""
+    L = lib()
+    ll = ctypes.c_longlong
+    L.tg_tile_shard.argtypes = [ll, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ll), ctypes.POINTER(ll),
+                                ctypes.POINTER(ll)]
+    L.tg_tile_shard.restype = ctypes.c_int
+    a, b, c = ll(0), ll(0), ll(0)
+    rc = L.tg_tile_shard(int(ntiles), int(rank), int(nranks), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if rc != TG_OK:
+        raise TGError(rc, "tg_tile_shard")
+    return a.value, b.value, c.value
 
 
 def tg_strerror(status):
@@ -231,7 +263,7 @@ class Basis:
         return X[:n.value].copy(), y[:n.value].copy(), e[:n.value].copy()
 
     def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
-               timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0):
+               timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0, shard_mode=0):
         """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
         torch CUDA tensors (then the densities and ``out`` stay on the device).  ``kernel``
         picks the class kernels: 0 per-class default, 1 one quartet per thread, 2 a thread
@@ -240,6 +272,7 @@ class Basis:
         opt = tg_options_default()
         opt.kernel_kind = int(kernel)
         opt.class_mask = int(class_mask)
+        opt.shard_mode = int(shard_mode)
         opt.screen_tol = float(screen_tol)
         opt.precision = int(precision)
         opt.rank, opt.nranks = int(rank), int(nranks)

@@ -7,18 +7,29 @@
 #include <cstdint>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
 #include <vector>
 
 #include "class_launchers.cuh"
+#include "plan_kernels.cuh"
 #include "router.cuh"
 #include "setup_kernels.cuh"
 
 using namespace tg;
 
 namespace {
+
+// Test hook for the allocation-failure path: while the environment variable
+// TDGRAD_FAIL_ALLOC is set to 1, every arena growth fails as if cudaMalloc had
+// run out of device memory (checked on the host; no CUDA call is made).
+bool alloc_failure_injected()
+{
+    const char *e = std::getenv("TDGRAD_FAIL_ALLOC");
+    return e && e[0] == '1' && e[1] == 0;
+}
 
 struct DevArena {
     char *p = nullptr;
@@ -27,6 +38,7 @@ struct DevArena {
     cudaError_t reserve(size_t bytes)
     {
         if (bytes <= cap) return cudaSuccess;
+        if (alloc_failure_injected()) return cudaErrorMemoryAllocation;
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
@@ -72,6 +84,7 @@ struct tg_basis {
     long long *d_bpoff = nullptr;  // per canonical pair key: offset of its primitive-pair bounds
     double *d_bp = nullptr;        // primitive-pair bounds b_kl (larger shell index first)
     DevArena ws1, ws2;
+    DevArena ws3, ws4;  // device tile planner: per-class tile maxima and rows; tile lists
     float *d_router = nullptr;  // router parameters, mean and std on the device
     int nsm = 0;
 };
@@ -111,6 +124,8 @@ void free_basis(tg_basis *b)
     cudaFree(b->d_bp);
     b->ws1.release();
     b->ws2.release();
+    b->ws3.release();
+    b->ws4.release();
 }
 
 int basis_setup(tg_basis *b, const double *xyz, const double *exps, const double *coefs)
@@ -222,6 +237,15 @@ void tg_options_default(tg_options *o)
 
 int tg_abi_version(void) { return TG_ABI_VERSION; }
 
+int tg_tile_shard(long long ntiles, int rank, int nranks, long long *first, long long *count, long long *stride)
+{
+    if (ntiles < 0 || nranks < 1 || rank < 0 || rank >= nranks || !first || !count || !stride) return TG_EINVAL;
+    *first = rank;
+    *stride = nranks;
+    *count = ntiles > rank ? (ntiles - rank + nranks - 1) / nranks : 0;
+    return TG_OK;
+}
+
 const char *tg_strerror(int s)
 {
     switch (s) {
@@ -325,6 +349,7 @@ struct Plan {
     double *d_Q = nullptr, *d_Qd = nullptr;
     std::vector<HostTile> tiles;
     int qc_P[NQC], qc_Q[NQC];
+    unsigned class_mask = 0;
     int launches = 0;
     int G = 1;
     PairSet set(int c) const
@@ -353,11 +378,12 @@ int check_pairs(int npair, const tg_pair *pairs, const tg_options &opt, double &
         opt.precision != TG_FP32)
         return TG_EINVAL;
     if (!(opt.mixed_tol >= 0.0) || !std::isfinite(opt.mixed_tol)) return TG_EINVAL;
-    if (opt.kernel_kind < TG_KERNEL_DEFAULT || opt.kernel_kind > TG_KERNEL_GROUP) return TG_EINVAL;
+    if (opt.kernel_kind < TG_KERNEL_DEFAULT || opt.kernel_kind > TG_KERNEL_WARP) return TG_EINVAL;
     if (opt.deterministic != 0 && opt.deterministic != 1) return TG_EINVAL;
     if (opt.class_mask >> NQC) return TG_EINVAL;
     for (int r : opt.reserved)
         if (r != 0) return TG_EINVAL;
+    if (opt.shard_mode != TG_SHARD_PAIR_KEY && opt.shard_mode != TG_SHARD_TILES) return TG_EINVAL;
     omega = 0.0;
     use_lr = 0;
     for (int p = 0; p < npair; ++p) {
@@ -375,7 +401,8 @@ int check_pairs(int npair, const tg_pair *pairs, const tg_options &opt, double &
 }
 
 // Densities, block factors, screened pairs, primitive pairs, unrouted tiles.
-int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &opt, cudaStream_t st, Plan &pl)
+int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &opt, cudaStream_t st, Plan &pl,
+              bool host_tiles = true)
 {
     double omega;
     int use_lr;
@@ -401,7 +428,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
     const int nmat_up = opt.device_ptrs ? 0 : 2 * npair;
     const size_t need1 = al(sizeof(double) * nbf2) * (nmat_up + 2 * npair) + al(sizeof(double) * (size_t)ns * ns) +
                          al(sizeof(double) * ns) + al(sizeof(double) * TG_MAX_PAIRS) +
-                         al(sizeof(double) * 3 * natom) + al(sizeof(unsigned long long) * 4 * NQC) + 4096;
+                         al(sizeof(double) * 3 * natom) + al(sizeof(unsigned long long) * NCNT * NQC) + 4096;
     TG_CUDA(W.reserve(need1));
     W.used = 0;
     double *dmat[2 * TG_MAX_PAIRS], *dS[2 * TG_MAX_PAIRS];
@@ -411,7 +438,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
     pl.dMrow = W.take<double>(ns);
     double *dw = W.take<double>(TG_MAX_PAIRS);
     pl.dgrad = W.take<double>(3 * natom);
-    pl.dcnt = W.take<unsigned long long>(4 * NQC);
+    pl.dcnt = W.take<unsigned long long>(NCNT * NQC);
     for (int p = 0; p < npair; ++p) {
         if (opt.device_ptrs) {
             den.A[p] = pairs[p].A;
@@ -488,7 +515,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
         for (int P = 0; P < NPC; ++P)
             for (int Qc = 0; Qc <= P; ++Qc)
                 ntl_max += (long long)((pl.cls[P].size() + TB - 1) / TB) * ((pl.cls[Qc].size() + TK - 1) / TK);
-        const size_t ntl = (size_t)std::max<long long>(ntl_max, 1);
+        const size_t ntl = host_tiles ? (size_t)std::max<long long>(ntl_max, 1) : 1;
         const size_t need2 = 6 * al(sizeof(int) * np_k) + 2 * al(sizeof(double) * np_k) +
                              6 * al(sizeof(double) * npp) + 12 * al(sizeof(float) * npp) + al(sizeof(uint4) * ntl) +
                              al(sizeof(MolDesc)) +
@@ -563,12 +590,14 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
         pl.nprimpairs = po;
     }
 
-    // ---- unrouted quartet tiles with their bounds (screened)
+    // ---- unrouted quartet tiles with their bounds (screened); the device
+    // planner (device_tiles) builds the same list on the GPU instead
     for (int P = 0; P < NPC; ++P)
         for (int Qc = 0; Qc <= P; ++Qc) {
             pl.qc_P[P * (P + 1) / 2 + Qc] = P;
             pl.qc_Q[P * (P + 1) / 2 + Qc] = Qc;
         }
+    pl.class_mask = opt.class_mask;
     auto blockmax = [&](int c, int blk, int bsz, double &q, double &qd, double &m) {
         q = qd = m = 0.0;
         const int lo = blk * bsz, hi = std::min((int)pl.cls[c].size(), lo + bsz);
@@ -579,7 +608,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
             m = std::max(m, std::max(pl.Mrow[hp.sa], pl.Mrow[hp.sb]));
         }
     };
-    for (int qc = 0; qc < NQC; ++qc) {
+    for (int qc = 0; qc < NQC && host_tiles; ++qc) {
         if (opt.class_mask && !((opt.class_mask >> qc) & 1u)) continue;
         const int P = pl.qc_P[qc], Qc = pl.qc_Q[qc];
         const int nP = (int)pl.cls[P].size(), nQ = (int)pl.cls[Qc].size();
@@ -653,8 +682,9 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
     pl.scr.scale = scale;
     pl.scr.M = pl.dM;
     pl.scr.nshell = ns;
-    pl.scr.rank = opt.rank;
-    pl.scr.nranks = opt.nranks;
+    // the pair-key shard filter runs inside the class kernels; tile shards select tiles
+    pl.scr.rank = opt.shard_mode == TG_SHARD_TILES ? 0 : opt.rank;
+    pl.scr.nranks = opt.shard_mode == TG_SHARD_TILES ? 1 : opt.nranks;
     return TG_OK;
 }
 
@@ -717,9 +747,11 @@ int predict_tiles(tg_basis *b, const Plan &pl, const tg_router *r, const std::ve
 // at most nfq * bound, and a tile holds TILE quartets) for the bound router,
 // eps_rel * 10^(prediction + margin) for the learned router, whose prediction
 // is the tile's largest contribution to one gradient component.  Tiles go to
-// fp32 in increasing e_t while sum e_t^2 stays within (mixed_tol / 3)^2: the
-// fp32 rounding errors of different tiles are independent, so they add in
-// quadrature, and the factor 3 is the safety margin of that model.
+// fp32 in increasing e_t while sum e_t^2 stays within mixed_tol^2: the fp32
+// rounding errors of different tiles are independent, so they add in
+// quadrature.  The safety margin lives in the estimates themselves (the
+// bound router's rigorous bound; the learned router's margin, calibrated on
+// measured errors against fp64).
 int compute_route(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_t st, TileRef *d_ref, float *d_feat,
                   float *d_pred, std::vector<uint8_t> &route, int &launches)
 {
@@ -747,7 +779,7 @@ int compute_route(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream
         std::vector<size_t> ord(ntl);
         for (size_t i = 0; i < ntl; ++i) ord[i] = i;
         std::stable_sort(ord.begin(), ord.end(), [&](size_t u, size_t v) { return err[u] < err[v]; });
-        const double budget = (opt.mixed_tol / 3.0) * (opt.mixed_tol / 3.0);
+        const double budget = opt.mixed_tol * opt.mixed_tol;
         double acc = 0.0;
         for (size_t i : ord) {
             if (acc + err[i] * err[i] > budget) break;
@@ -755,6 +787,221 @@ int compute_route(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream
             route[i] = 1;
         }
     }
+    return TG_OK;
+}
+
+// Tile lists of one call built on the device (row a3 of the hot path): tile
+// maxima per class, the hierarchical block screen (plan_kernels.cu) counting
+// and then writing the kept tiles of every (class, bra tile) row, fp32 /
+// fp64 routing from a histogram of the tiles' error estimates, and an
+// order-preserving split into the (class, precision) launch lists.  The host
+// only prefix-sums per-row counts and picks the routing cut-off from the
+// histogram.  Routing: tiles go to fp32 bin by bin in increasing error while
+// the sum of e_t^2, each e_t taken at its bin's upper edge, stays within
+// mixed_tol^2 -- the rule of compute_route, with bins of 2^(1/8).
+struct DevTiles {
+    uint4 *tiles = nullptr;  // launch lists, [class][fp64 | fp32]
+    long long off[2 * NQC + 1];
+    long long ntiles = 0;
+    int cut = 0;
+};
+
+int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_t st, DevTiles &dt, int &launches)
+{
+    // rows (class, bra tile, ket tile run): the ket tiles of a class split into
+    // runs of equal cost factor (primitive pairs of a tile's first pair; the
+    // pairs are sorted by it), every row of a class has one cost, and the rows
+    // of a class are sorted stably by decreasing cost -- the tile order of the
+    // host planner (build_exec)
+    std::vector<int4> rows;
+    int row_qc_begin[NQC + 1];
+    {
+        std::vector<std::vector<int2>> runs(NPC);  // (first ket tile, end) per pair class
+        for (int c = 0; c < NPC; ++c) {
+            const int n = (int)pl.cls[c].size(), nk = (n + TK - 1) / TK;
+            for (int kt = 0; kt < nk;) {
+                int e = kt + 1;
+                while (e < nk && pl.cls[c][e * TK].np == pl.cls[c][kt * TK].np) ++e;
+                runs[c].push_back(make_int2(kt, e));
+                kt = e;
+            }
+        }
+        std::vector<std::pair<long long, int4>> tmp;
+        for (int qc = 0; qc < NQC; ++qc) {
+            row_qc_begin[qc] = (int)rows.size();
+            if (pl.class_mask && !((pl.class_mask >> qc) & 1u)) continue;
+            const int P = pl.qc_P[qc], Qc = pl.qc_Q[qc];
+            const int nP = (int)pl.cls[P].size(), nQ = (int)pl.cls[Qc].size();
+            if (!nP || !nQ) continue;
+            tmp.clear();
+            for (int bt = 0; bt < (nP + TB - 1) / TB; ++bt) {
+                const long long cb = pl.cls[P][bt * TB].np;
+                const int lim = P == Qc ? (bt * TB + TB - 1) / TK + 1 : (nQ + TK - 1) / TK;  // canonical limit
+                for (const int2 &ru : runs[Qc]) {
+                    if (ru.x >= lim) break;
+                    tmp.push_back({cb * pl.cls[Qc][ru.x * TK].np, make_int4(qc, bt, ru.x, std::min(ru.y, lim))});
+                }
+            }
+            std::stable_sort(tmp.begin(), tmp.end(),
+                             [](const std::pair<long long, int4> &u, const std::pair<long long, int4> &v) {
+                                 return u.first > v.first;
+                             });
+            for (auto &t : tmp) rows.push_back(t.second);
+        }
+        row_qc_begin[NQC] = (int)rows.size();
+    }
+    const int nrows = (int)rows.size();
+    for (int k = 0; k <= 2 * NQC; ++k) dt.off[k] = 0;
+    dt.ntiles = 0;
+    if (!nrows) return TG_OK;
+    // ---- phase A buffers: tile maxima, rows, per-row counts and offsets
+    RowArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.nrows = nrows;
+    ra.tau = pl.tau;
+    ra.scale = pl.scale;
+    for (int qc = 0; qc < NQC; ++qc) {
+        ra.qcP[qc] = pl.qc_P[qc];
+        ra.qcQ[qc] = pl.qc_Q[qc];
+    }
+    size_t needA = al(sizeof(int4) * nrows) + 3 * al(sizeof(int) * (nrows + 1)) +
+                   3 * al(sizeof(long long) * (nrows + 1)) + al(sizeof(unsigned long long) * RBIN_N) + 4096;
+    for (int c = 0; c < NPC; ++c) {
+        const size_t n = pl.cls[c].size();
+        const size_t nb = (n + TB - 1) / TB, nk = (n + TK - 1) / TK, ng = (nk + GROUP - 1) / GROUP;
+        needA += 3 * (al(sizeof(double) * std::max<size_t>(nb, 1)) + al(sizeof(double) * std::max<size_t>(nk, 1)) +
+                      al(sizeof(double) * std::max<size_t>(ng, 1)));
+    }
+    DevArena &A = b->ws3;
+    TG_CUDA(A.reserve(needA));
+    A.used = 0;
+    for (int c = 0; c < NPC; ++c) {
+        const int n = (int)pl.cls[c].size();
+        const int nb = (n + TB - 1) / TB, nk = (n + TK - 1) / TK, ng = (nk + GROUP - 1) / GROUP;
+        TileMaxima &t = ra.t[c];
+        double *bq = A.take<double>(std::max(nb, 1)), *bqd = A.take<double>(std::max(nb, 1)),
+               *bm = A.take<double>(std::max(nb, 1));
+        double *kq = A.take<double>(std::max(nk, 1)), *kqd = A.take<double>(std::max(nk, 1)),
+               *km = A.take<double>(std::max(nk, 1));
+        double *gq = A.take<double>(std::max(ng, 1)), *gqd = A.take<double>(std::max(ng, 1)),
+               *gm = A.take<double>(std::max(ng, 1));
+        t.bq = bq; t.bqd = bqd; t.bm = bm; t.kq = kq; t.kqd = kqd; t.km = km; t.gq = gq; t.gqd = gqd; t.gm = gm;
+        t.nbt = nb;
+        t.nkt = nk;
+        if (!n) continue;
+        const PairSet ps = pl.set(c);
+        k_tile_maxima<<<(nb + 127) / 128, 128, 0, st>>>(n, TB, ps.sa, ps.sb, ps.Q, ps.Qd, pl.dMrow, bq, bqd, bm);
+        k_tile_maxima<<<(nk + 127) / 128, 128, 0, st>>>(n, TK, ps.sa, ps.sb, ps.Q, ps.Qd, pl.dMrow, kq, kqd, km);
+        k_group_maxima<<<(ng + 127) / 128, 128, 0, st>>>(nk, kq, kqd, km, gq, gqd, gm);
+        launches += 3;
+    }
+    int4 *d_rows = A.take<int4>(nrows);
+    int *d_cnt = A.take<int>(nrows + 1), *d_cnt32 = A.take<int>(nrows + 1);
+    long long *d_off = A.take<long long>(nrows + 1), *d_o64 = A.take<long long>(nrows + 1),
+              *d_o32 = A.take<long long>(nrows + 1);
+    unsigned long long *d_hist = A.take<unsigned long long>(RBIN_N);
+    ra.rows = d_rows;
+    TG_CUDA(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int4) * nrows, cudaMemcpyHostToDevice, st));
+    const unsigned gr = (unsigned)((nrows + 127) / 128);
+    k_tile_rows<<<gr, 128, 0, st>>>(ra, 0, d_cnt, nullptr, nullptr, nullptr);
+    ++launches;
+    TG_CUDA(cudaGetLastError());
+    std::vector<int> cnt(nrows);
+    TG_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * nrows, cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaStreamSynchronize(st));
+    std::vector<long long> off(nrows + 1);
+    off[0] = 0;
+    for (int r = 0; r < nrows; ++r) off[r + 1] = off[r] + cnt[r];
+    const long long ntl = off[nrows];
+    dt.ntiles = ntl;
+    if (!ntl) return TG_OK;
+    TG_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (nrows + 1), cudaMemcpyHostToDevice, st));
+    // ---- phase B buffers: the tiles, their bounds, routing bins, launch lists
+    const bool learned = opt.precision == TG_MIXED_LEARNED, bound = opt.precision == TG_MIXED_BOUND;
+    size_t needB = 2 * al(sizeof(uint4) * ntl) + al(sizeof(float) * ntl) + al(sizeof(int) * ntl) + 4096;
+    if (learned) needB += al(sizeof(TileRef) * ntl) + al(sizeof(float) * ntl * NFEAT) + al(sizeof(float) * ntl);
+    DevArena &B = b->ws4;
+    TG_CUDA(B.reserve(needB));
+    B.used = 0;
+    uint4 *d_raw = B.take<uint4>(ntl), *d_out = B.take<uint4>(ntl);
+    float *d_bnd = B.take<float>(ntl);
+    int *d_bin = B.take<int>(ntl);
+    k_tile_rows<<<gr, 128, 0, st>>>(ra, 1, nullptr, d_off, d_raw, d_bnd);
+    ++launches;
+    TG_CUDA(cudaGetLastError());
+    const unsigned gt = (unsigned)((ntl + 127) / 128);
+    int cut = 0;
+    const int *bins = nullptr;
+    if (opt.precision == TG_FP32) {
+        cut = 1;
+    } else if (bound || learned) {
+        TG_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * RBIN_N, st));
+        if (bound) {
+            k_route_bins<<<gt, 128, 0, st>>>(ntl, d_raw, d_bnd, 0, kEps32Bound * TILE, 0.0, ra, d_bin, d_hist);
+            ++launches;
+        } else {
+            TileRef *d_ref = B.take<TileRef>(ntl);
+            float *d_feat = B.take<float>(ntl * NFEAT), *d_pred = B.take<float>(ntl);
+            k_tile_refs<<<gt, 128, 0, st>>>(ntl, d_raw, ra, d_ref);
+            k_tile_features<<<gt, 128, 0, st>>>((int)ntl, d_ref, feature_args(b, pl), d_feat);
+            const tg_router *r = opt.router;
+            float *dparams = b->d_router;
+            TG_CUDA(cudaMemcpyAsync(dparams, r->params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, st));
+            TG_CUDA(cudaMemcpyAsync(dparams + NPARAM, r->mu, sizeof(float) * NFEAT, cudaMemcpyHostToDevice, st));
+            TG_CUDA(cudaMemcpyAsync(dparams + NPARAM + NFEAT, r->sd, sizeof(float) * NFEAT, cudaMemcpyHostToDevice,
+                                    st));
+            k_mlp_predict<<<gt, 128, 0, st>>>((int)ntl, d_feat, dparams + NPARAM, dparams + NPARAM + NFEAT, dparams,
+                                             d_pred);
+            k_route_bins<<<gt, 128, 0, st>>>(ntl, d_raw, d_pred, 1, (double)r->eps_rel, (double)r->margin, ra, d_bin,
+                                             d_hist);
+            launches += 4;
+        }
+        TG_CUDA(cudaGetLastError());
+        std::vector<unsigned long long> hist(RBIN_N);
+        TG_CUDA(cudaMemcpyAsync(hist.data(), d_hist, sizeof(unsigned long long) * RBIN_N, cudaMemcpyDeviceToHost, st));
+        TG_CUDA(cudaStreamSynchronize(st));
+        const double budget = opt.mixed_tol * opt.mixed_tol;
+        double acc = 0.0;
+        for (int k = 0; k < RBIN_N; ++k) {
+            const double u = route_bin_upper(k);
+            const double add = (double)hist[k] * u * u;
+            if (acc + add > budget) break;
+            acc += add;
+            cut = k + 1;
+        }
+        bins = d_bin;
+    }
+    dt.cut = cut;
+    // ---- order-preserving split into the (class, precision) lists
+    k_row_fp32_count<<<gr, 128, 0, st>>>(nrows, d_off, bins, cut, d_cnt32);
+    ++launches;
+    TG_CUDA(cudaGetLastError());
+    std::vector<int> c32(nrows);
+    TG_CUDA(cudaMemcpyAsync(c32.data(), d_cnt32, sizeof(int) * nrows, cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaStreamSynchronize(st));
+    std::vector<long long> o64(nrows), o32(nrows);
+    long long pos = 0;
+    for (int qc = 0; qc < NQC; ++qc) {
+        dt.off[2 * qc] = pos;
+        for (int r = row_qc_begin[qc]; r < row_qc_begin[qc + 1]; ++r) {
+            o64[r] = pos;
+            pos += cnt[r] - c32[r];
+        }
+        dt.off[2 * qc + 1] = pos;
+        for (int r = row_qc_begin[qc]; r < row_qc_begin[qc + 1]; ++r) {
+            o32[r] = pos;
+            pos += c32[r];
+        }
+    }
+    dt.off[2 * NQC] = pos;
+    TG_CUDA(cudaMemcpyAsync(d_o64, o64.data(), sizeof(long long) * nrows, cudaMemcpyHostToDevice, st));
+    TG_CUDA(cudaMemcpyAsync(d_o32, o32.data(), sizeof(long long) * nrows, cudaMemcpyHostToDevice, st));
+    k_row_scatter<<<gr, 128, 0, st>>>(nrows, d_off, d_raw, bins, cut, d_o64, d_o32, d_out);
+    ++launches;
+    TG_CUDA(cudaGetLastError());
+    // the host vectors must outlive the asynchronous copies
+    TG_CUDA(cudaStreamSynchronize(st));
+    dt.tiles = d_out;
     return TG_OK;
 }
 
@@ -826,7 +1073,8 @@ void build_exec(const std::vector<const Plan *> &plans, const std::vector<std::v
 // components go to dump[(list position * TILE + thread) * 12 + c].
 int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, double *d_part,
                 unsigned long long *dcnt, double *dump, const double *boys, int G, const int *grids, bool timing,
-                cudaStream_t st, tg_stats *stats, int &launches, const int *kinds = nullptr, int kind_all = 0)
+                cudaStream_t st, tg_stats *stats, int &launches, const int *kinds = nullptr, int kind_all = 0,
+                int tile_rank = 0, int tile_nranks = 1)
 {
     OutArgs out;
     out.partials = d_part;
@@ -845,7 +1093,9 @@ int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, dou
     for (int qc = 0; qc < NQC && rc == TG_OK; ++qc) {
         for (int r = 0; r < 2; ++r) {
             const int k = 2 * qc + r;
-            const long long nt = ex.off[k + 1] - ex.off[k];
+            // tile-cyclic shard: tiles tile_rank, tile_rank + tile_nranks, ... of the list
+            long long first = 0, nt = 0, stride = 1;
+            tg_tile_shard(ex.off[k + 1] - ex.off[k], tile_rank, tile_nranks, &first, &nt, &stride);
             if (nt <= 0) continue;
             ClassLaunch cl;
             int Pc = 0, Qc = 0;
@@ -858,11 +1108,12 @@ int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, dou
             cl.P = Pc;
             cl.Q = Qc;
             cl.ntiles = nt;
-            cl.tiles = d_tiles + ex.off[k];
+            cl.tiles = d_tiles + ex.off[k] + first;
+            cl.stride = stride;
             cl.nsplit = cl.nchunk = 1;
             cl.kind = kinds ? kinds[k] : kind_all;
             OutArgs o = out;
-            o.counters = dcnt + 4 * qc;
+            o.counters = dcnt + NCNT * qc;
             if (dump) o.dump = dump + (size_t)ex.off[k] * TILE * 12;
             const int grid = std::min(G, (grids && grids[k] > 0) ? grids[k] : G);  // cap; the launcher sizes it
             if (timing) cudaEventRecord(e0, st);
@@ -885,17 +1136,50 @@ int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, dou
     return rc;
 }
 
-void fill_stats(tg_stats *stats, const unsigned long long *hc, long long pairs, long long tiles, int launches, int G)
+// fp64 / fp32 FMA peaks of the current device (FLOP/s): SMs x (2 | 128) FMA
+// per clock per SM x 2 x the SM clock
+void alu_peaks(double &p64, double &p32)
+{
+    int dev = 0, nsm = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+        cudaGetLastError();
+        p64 = p32 = 0.0;
+        return;
+    }
+    p64 = (double)nsm * 2.0 * 2.0 * khz * 1e3;
+    p32 = (double)nsm * 128.0 * 2.0 * khz * 1e3;
+}
+
+void fill_stats(tg_stats *stats, const unsigned long long *hc, long long pairs, long long tiles, int launches, int G,
+                int nops = 2)
 {
     if (!stats) return;
+    double f64 = 0.0, f32 = 0.0, ms64 = 0.0, ms32 = 0.0;
+    for (int qc = 0; qc < NQC; ++qc) {
+        double fpq, fp;
+        class_flops(qc, nops, &fpq, &fp);
+        f64 += fpq * (double)hc[NCNT * qc + 1] + fp * (double)hc[NCNT * qc + 4];
+        f32 += fpq * (double)hc[NCNT * qc + 3] + fp * (double)hc[NCNT * qc + 5];
+        ms64 += stats->class_ms[qc];
+        ms32 += stats->class_ms_fp32[qc];
+    }
+    stats->fp64_flop = f64;
+    stats->fp32_flop = f32;
+    double p64 = 0.0, p32 = 0.0;
+    if (ms64 > 0.0 || ms32 > 0.0) alu_peaks(p64, p32);
+    stats->fp64_frac_peak = (ms64 > 0.0 && p64 > 0.0) ? f64 / (ms64 * 1e-3) / p64 : 0.0;
+    stats->fp32_frac_peak = (ms32 > 0.0 && p32 > 0.0) ? f32 / (ms32 * 1e-3) / p32 : 0.0;
     long long q = 0, pq = 0, q32 = 0;
     for (int qc = 0; qc < NQC; ++qc) {
-        stats->class_quartets[qc] = (long long)hc[4 * qc];
-        stats->class_prim_quartets[qc] = (long long)hc[4 * qc + 1];
-        stats->class_prim_quartets_fp32[qc] = (long long)hc[4 * qc + 3];
-        q += (long long)hc[4 * qc];
-        pq += (long long)hc[4 * qc + 1] + (long long)hc[4 * qc + 3];
-        q32 += (long long)hc[4 * qc + 2];
+        stats->class_quartets[qc] = (long long)hc[NCNT * qc];
+        stats->class_prim_quartets[qc] = (long long)hc[NCNT * qc + 1];
+        stats->class_prim_quartets_fp32[qc] = (long long)hc[NCNT * qc + 3];
+        stats->class_bra_prims[qc] = (long long)hc[NCNT * qc + 4];
+        stats->class_bra_prims_fp32[qc] = (long long)hc[NCNT * qc + 5];
+        q += (long long)hc[NCNT * qc];
+        pq += (long long)hc[NCNT * qc + 1] + (long long)hc[NCNT * qc + 3];
+        q32 += (long long)hc[NCNT * qc + 2];
     }
     stats->quartets = q;
     stats->prim_quartets = pq;
@@ -946,45 +1230,44 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
     if (opt.precision == TG_MIXED_LEARNED && (!opt.router || !opt.router->trained)) return TG_EROUTER;
     cudaStream_t st = (cudaStream_t)opt.stream;
     Plan pl;
-    int rc = make_plan(b, npair, pairs, opt, st, pl);
+    int rc = make_plan(b, npair, pairs, opt, st, pl, false);
     if (rc != TG_OK) return rc;
     const int natom = b->natom;
     int launches = pl.launches;
-    const size_t ntl = pl.tiles.size();
     DevArena &V = b->ws2;
-    uint4 *d_tiles = V.take<uint4>(std::max<size_t>(ntl, 1));
-    TileRef *d_ref = V.take<TileRef>(std::max<size_t>(ntl, 1));
-    float *d_feat = V.take<float>(std::max<size_t>(ntl, 1) * NFEAT);
-    float *d_pred = V.take<float>(std::max<size_t>(ntl, 1));
     double *d_part = V.take<double>((size_t)pl.G * 3 * natom);
     MolDesc *d_mol = V.take<MolDesc>(1);
-    std::vector<std::vector<uint8_t>> routes(1);
-    rc = compute_route(b, pl, opt, st, d_ref, d_feat, d_pred, routes[0], launches);
+    // the screened tile lists, routed and split per (class, precision), built on the device
+    DevTiles dt;
+    rc = device_tiles(b, pl, opt, st, dt, launches);
     if (rc != TG_OK) return rc;
+    const size_t ntl = (size_t)dt.ntiles;
     Exec ex;
-    build_exec({&pl}, routes, nullptr, ex);
+    for (int k = 0; k <= 2 * NQC; ++k) ex.off[k] = dt.off[k];
     ex.natom_total = ex.natom_max = natom;
+    const uint4 *d_tiles = dt.tiles;
     const MolDesc md = make_desc(pl, 0);
     TG_CUDA(cudaMemcpyAsync(d_mol, &md, sizeof(MolDesc), cudaMemcpyHostToDevice, st));
-    if (!ex.tiles.empty())
-        TG_CUDA(cudaMemcpyAsync(d_tiles, ex.tiles.data(), sizeof(uint4) * ex.tiles.size(), cudaMemcpyHostToDevice, st));
     TG_CUDA(cudaMemsetAsync(d_part, 0, sizeof(double) * (size_t)pl.G * 3 * natom, st));
-    TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 4 * NQC, st));
+    TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * NCNT * NQC, st));
     if (stats)
         for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
+    const double plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, nullptr, b->d_boys, pl.G, nullptr, opt.timing != 0, st,
-                     stats, launches, nullptr, opt.kernel_kind);
+                     stats, launches, nullptr, opt.kernel_kind, opt.shard_mode == TG_SHARD_TILES ? opt.rank : 0,
+                     opt.shard_mode == TG_SHARD_TILES ? opt.nranks : 1);
     if (rc != TG_OK) return rc;
     k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, pl.G, d_part, pl.dgrad);
     ++launches;
     TG_CUDA(cudaGetLastError());
-    unsigned long long hc[4 * NQC];
+    unsigned long long hc[NCNT * NQC];
     TG_CUDA(cudaMemcpyAsync(hc, pl.dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
     TG_CUDA(cudaMemcpyAsync(grad, pl.dgrad, sizeof(double) * 3 * natom,
                             opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     TG_CUDA(cudaStreamSynchronize(st));
     if (stats) {
-        fill_stats(stats, hc, pl.npairs_kept, (long long)ntl, launches, pl.G);
+        fill_stats(stats, hc, pl.npairs_kept, (long long)ntl, launches, pl.G, pl.den.use_lr ? 2 : 1);
+        stats->plan_ms = plan_ms;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return TG_OK;
@@ -1040,7 +1323,7 @@ int tg_tile_samples(const tg_basis *cb, int npair, const tg_pair *pairs, const t
         build_exec({&pl}, routes, &subset, ex);
         ex.natom_total = ex.natom_max = b->natom;
         TG_CUDA(cudaMemcpyAsync(d_tiles, ex.tiles.data(), sizeof(uint4) * ex.tiles.size(), cudaMemcpyHostToDevice, st));
-        TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * 4 * NQC, st));
+        TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * NCNT * NQC, st));
         // the dump is written at list positions; lists are class-major with r fixed,
         // so positions run over the samples in class order
         rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, r ? d32 : d64, b->d_boys, pl.G, nullptr, false, st,
@@ -1149,14 +1432,14 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
     const size_t ntl = std::max<size_t>(bt->ex.tiles.size(), 1);
     const size_t need = al(sizeof(MolDesc) * nmol) + al(sizeof(uint4) * ntl) +
                         al(sizeof(double) * (size_t)G * 3 * natom_total) + al(sizeof(double) * 3 * natom_total) +
-                        al(sizeof(unsigned long long) * 4 * NQC) + 4096;
+                        al(sizeof(unsigned long long) * NCNT * NQC) + 4096;
     TG_CUDA(bt->arena.reserve(need));
     bt->arena.used = 0;
     bt->d_mols = bt->arena.take<MolDesc>(nmol);
     bt->d_tiles = bt->arena.take<uint4>(ntl);
     bt->d_part = bt->arena.take<double>((size_t)G * 3 * natom_total);
     bt->d_grad = bt->arena.take<double>(3 * natom_total);
-    bt->d_cnt = bt->arena.take<unsigned long long>(4 * NQC);
+    bt->d_cnt = bt->arena.take<unsigned long long>(NCNT * NQC);
     std::vector<MolDesc> mds(nmol);
     for (int m = 0; m < nmol; ++m) mds[m] = make_desc(bt->plans[m], bt->atom_off[m]);
     TG_CUDA(cudaMemcpy(bt->d_mols, mds.data(), sizeof(MolDesc) * nmol, cudaMemcpyHostToDevice));
@@ -1211,14 +1494,14 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
         bt->arena.release();
         const size_t need2 = al(sizeof(MolDesc) * nmol) + al(sizeof(uint4) * ntl) +
                              al(sizeof(double) * (size_t)G * 3 * natom_total) + al(sizeof(double) * 3 * natom_total) +
-                             al(sizeof(unsigned long long) * 4 * NQC) + 4096;
+                             al(sizeof(unsigned long long) * NCNT * NQC) + 4096;
         TG_CUDA(bt->arena.reserve(need2));
         bt->arena.used = 0;
         bt->d_mols = bt->arena.take<MolDesc>(nmol);
         bt->d_tiles = bt->arena.take<uint4>(ntl);
         bt->d_part = bt->arena.take<double>((size_t)G * 3 * natom_total);
         bt->d_grad = bt->arena.take<double>(3 * natom_total);
-        bt->d_cnt = bt->arena.take<unsigned long long>(4 * NQC);
+        bt->d_cnt = bt->arena.take<unsigned long long>(NCNT * NQC);
         TG_CUDA(cudaMemcpy(bt->d_mols, mds.data(), sizeof(MolDesc) * nmol, cudaMemcpyHostToDevice));
         if (!bt->ex.tiles.empty())
             TG_CUDA(cudaMemcpy(bt->d_tiles, bt->ex.tiles.data(), sizeof(uint4) * bt->ex.tiles.size(),
@@ -1231,7 +1514,7 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
         if (pass == 1) TG_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
         int n = 0;
         cudaMemsetAsync(bt->d_part, 0, sizeof(double) * (size_t)G * 3 * natom_total, bt->cap);
-        cudaMemsetAsync(bt->d_cnt, 0, sizeof(unsigned long long) * 4 * NQC, bt->cap);
+        cudaMemsetAsync(bt->d_cnt, 0, sizeof(unsigned long long) * NCNT * NQC, bt->cap);
         int rc = launch_exec(bt->ex, bt->d_mols, bt->d_tiles, bt->d_part, bt->d_cnt, nullptr, boys, G,
                              bt->grids.data(), false, bt->cap, nullptr, n, bt->kinds.data());
         k_reduce<<<(3 * natom_total + 127) / 128, 128, 0, bt->cap>>>(3 * natom_total, G, bt->d_part, bt->d_grad);
@@ -1263,7 +1546,7 @@ int tg_batch_run(tg_batch *bt, double *const *grads, const tg_options *opt_in, t
     for (int m = 0; m < bt->nmol; ++m)
         if (!grads[m]) return TG_EINVAL;
     TG_CUDA(cudaGraphLaunch(bt->gexec, st));
-    unsigned long long hc[4 * NQC];
+    unsigned long long hc[NCNT * NQC];
     TG_CUDA(cudaMemcpyAsync(hc, bt->d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
     for (int m = 0; m < bt->nmol; ++m) {
         TG_CUDA(cudaMemcpyAsync(grads[m], bt->d_grad + 3 * (size_t)bt->atom_off[m],
@@ -1272,8 +1555,12 @@ int tg_batch_run(tg_batch *bt, double *const *grads, const tg_options *opt_in, t
     }
     TG_CUDA(cudaStreamSynchronize(st));
     if (stats) {
-        fill_stats(stats, hc, bt->pairs, (long long)bt->ex.tiles.size(), bt->launches, bt->G);
         for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
+        int nops = 1;
+        for (const Plan &pl : bt->plans)
+            if (pl.den.use_lr) nops = 2;
+        fill_stats(stats, hc, bt->pairs, (long long)bt->ex.tiles.size(), bt->launches, bt->G, nops);
+        stats->plan_ms = 0.0;  // planned at tg_batch_create
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return TG_OK;

@@ -1,5 +1,5 @@
 // (dp|dp) derivative-ERI class kernel instance.
-#include "eri_coop.cuh"
+#include "eri_warp.cuh"
 
 namespace tg {
 

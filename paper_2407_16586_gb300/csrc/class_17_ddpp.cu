@@ -1,5 +1,5 @@
 // (dd|pp) derivative-ERI class kernel instance.
-#include "eri_coop.cuh"
+#include "eri_warp.cuh"
 
 namespace tg {
 

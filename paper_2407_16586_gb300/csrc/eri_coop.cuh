@@ -465,14 +465,14 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
     const int grp = threadIdx.x / GS, lane = threadIdx.x % GS, bar = 1 + grp;
     double *slab = out.partials + (size_t)blockIdx.x * out.natom_total * 3;
     int cur = -1, cur_off3 = 0, cur_n3 = 0;
-    unsigned long long nq = 0, npq = 0;
+    unsigned long long nq = 0, npq = 0, nbv = 0;
     // unit = (tile, chunk, split): chunk c holds quartets c * QPC ... of the
     // tile, split s takes the bra primitive pairs s, s + S, ...
     const int S = cl.nsplit, C = cl.nchunk, QPC = TILE / C;
     for (long long it = blockIdx.x; it < cl.ntiles * C * S; it += gridDim.x) {
         const long long tile = it / (C * S);
         const int chunk = (int)((it / S) % C), split = (int)(it % S);
-        const uint4 tl = cl.tiles[tile];
+        const uint4 tl = cl.tiles[tile * cl.stride];
         const int mol = (int)tl.x;
         if (mol != cur) {
             if (out.use_smem) {
@@ -555,6 +555,7 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
                     at[3] = geo.sh_atom[sd];
                     if (split == 0) nq += 1;
                     npq += (unsigned long long)((nbp - split + S - 1) / S) * nkp;
+                    nbv += (unsigned long long)((nbp - split + S - 1) / S);
                 }
                 group_sync(bar, GS);
             }
@@ -581,10 +582,12 @@ __global__ void __launch_bounds__(TILE) k_grad_coop(const MolDesc *__restrict__ 
     for (int o = 16; o > 0; o >>= 1) {
         nq += __shfl_xor_sync(0xffffffffu, nq, o);
         npq += __shfl_xor_sync(0xffffffffu, npq, o);
+        nbv += __shfl_xor_sync(0xffffffffu, nbv, o);
     }
     if ((threadIdx.x & 31) == 0 && (nq || npq)) {  // a split unit may hold primitives only
         atomicAdd(out.counters + 0, nq);
         atomicAdd(out.counters + (sizeof(F) == 4 ? 3 : 1), npq);
+        atomicAdd(out.counters + (sizeof(F) == 4 ? 5 : 4), nbv);
         if (sizeof(F) == 4) atomicAdd(out.counters + 2, nq);
     }
 }
@@ -603,23 +606,6 @@ struct CoopChoice {
 
 namespace tg {
 
-// Kernel kind per class: the cooperative kernel is compiled for the fp64
-// classes with at least 54 function quartets and the fp32 classes with at
-// least 648, the thread kernel for every class below 648 (above, its
-// per-thread arrays run to tens of KB of local memory).  By default the
-// cooperative kernel runs for the fp64 classes where it measured faster on
-// GB300, (dp|ds) and every class from 216 function quartets on, and wherever
-// it is the only one.  ClassLaunch::kind = 1 / 2 forces the
-// thread / cooperative kernel where both exist.
-template <int LA, int LB, int LC, int LD>
-struct UseCoop {
-    static constexpr int nfq = ncart(LA) * ncart(LB) * ncart(LC) * ncart(LD);
-    static constexpr bool fp64 = nfq >= 54;
-    static constexpr bool fp32 = nfq >= 648;
-    static constexpr bool thread = nfq < 648;
-    static constexpr bool fp64_default = nfq >= 216 || (LA == 2 && LB == 1 && LC == 2 && LD == 0);
-};
-
 template <int LA, int LB, int LC, int LD, typename F>
 cudaError_t launch_coop(int gcap, size_t smem, cudaStream_t st, const MolDesc *mols, const ClassLaunch &cl,
                         const OutArgs &out, const double *boys)
@@ -627,26 +613,6 @@ cudaError_t launch_coop(int gcap, size_t smem, cudaStream_t st, const MolDesc *m
     using C = CoopChoice<LA, LB, LC, LD, F>;
     return launch_units(k_grad_coop<LA, LB, LC, LD, F, C::GS>, TILE / C::GS, gcap, smem + C::bytes_all(), st, mols,
                         cl, out, boys);
-}
-
-template <int LA, int LB, int LC, int LD>
-cudaError_t launch_class_kernel(int fp32, int gcap, size_t smem, cudaStream_t st, const MolDesc *mols,
-                                const ClassLaunch &cl, const OutArgs &out, const double *boys)
-{
-    using U = UseCoop<LA, LB, LC, LD>;
-    if (fp32) {
-        if constexpr (U::fp32) {
-            if (!U::thread || cl.kind != 1)
-                return launch_coop<LA, LB, LC, LD, float>(gcap, smem, st, mols, cl, out, boys);
-        }
-    } else {
-        if constexpr (U::fp64) {
-            if (!U::thread || cl.kind == 2 || (cl.kind == 0 && U::fp64_default))
-                return launch_coop<LA, LB, LC, LD, double>(gcap, smem, st, mols, cl, out, boys);
-        }
-    }
-    if constexpr (U::thread) return launch_thread_kernel<LA, LB, LC, LD>(fp32, gcap, smem, st, mols, cl, out, boys);
-    return cudaErrorInvalidValue;  // not reached: classes without a thread kernel return above
 }
 
 }  // namespace tg

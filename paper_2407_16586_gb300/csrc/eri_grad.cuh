@@ -774,13 +774,13 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
     int *ratom = reinterpret_cast<int *>(red + 6 * (TB + TK));
     double *slab = out.partials + (size_t)blockIdx.x * out.natom_total * 3;
     int cur = -1, cur_off3 = 0, cur_n3 = 0;
-    unsigned long long nq = 0, npq = 0;
+    unsigned long long nq = 0, npq = 0, nbv = 0;
     // unit = (tile, split): split s takes the bra primitive pairs s, s + S, ...
     const int S = cl.nsplit;
     for (long long it = blockIdx.x; it < cl.ntiles * S; it += gridDim.x) {
         const long long tile = it / S;
         const int split = (int)(it % S);
-        const uint4 tl = cl.tiles[tile];
+        const uint4 tl = cl.tiles[tile * cl.stride];
         const int mol = (int)tl.x;
         if (mol != cur) {
             if (out.use_smem) {
@@ -829,6 +829,7 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
                 at[3] = geo.sh_atom[sd];
                 if (split == 0) nq += 1;
                 npq += (unsigned long long)((nbp - split + S - 1) / S) * nkp;
+                nbv += (unsigned long long)((nbp - split + S - 1) / S);
             }
         }
         if (out.dump) {  // dump mode runs with one split per tile
@@ -852,10 +853,12 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
     for (int o = 16; o > 0; o >>= 1) {
         nq += __shfl_xor_sync(0xffffffffu, nq, o);
         npq += __shfl_xor_sync(0xffffffffu, npq, o);
+        nbv += __shfl_xor_sync(0xffffffffu, nbv, o);
     }
     if ((threadIdx.x & 31) == 0 && (nq || npq)) {  // a split unit may hold primitives only
         atomicAdd(out.counters + 0, nq);
         atomicAdd(out.counters + (FP32 ? 3 : 1), npq);
+        atomicAdd(out.counters + (FP32 ? 5 : 4), nbv);
         if (FP32) atomicAdd(out.counters + 2, nq);
     }
 }

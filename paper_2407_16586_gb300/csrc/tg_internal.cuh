@@ -13,6 +13,10 @@ constexpr int NQC = 21;  // quartet classes (bra pair class >= ket pair class), 
 constexpr int TB = 16;   // bra pairs per tile
 constexpr int TK = 8;    // ket pairs per tile
 constexpr int TILE = TB * TK;
+// per-class counters: [0] quartets, [1] fp64 primitive quartets, [2] fp32
+// quartets, [3] fp32 primitive quartets, [4] / [5] fp64 / fp32 bra primitive
+// pairs visited (one per quartet and bra primitive pair of a unit)
+constexpr int NCNT = 6;
 
 // Boys table: F_m(T0) on T0 = 0, 0.05, ..., 36 for m = 0..BOYS_M.
 constexpr int BOYS_M = 16;
@@ -93,7 +97,8 @@ struct MolDesc {
 struct ClassLaunch {
     int P, Q;                  // bra and ket pair classes (same list iff P == Q)
     long long ntiles;
-    const uint4 *tiles;        // (molecule, bra tile, ket tile, 0), grouped by molecule
+    const uint4 *tiles;        // (molecule, bra tile, ket tile, 0), grouped by molecule; tile t at tiles[t * stride]
+    long long stride;          // 1, or nranks for tile-cyclic shards
     int nsplit;                // units per tile along the bra primitive pairs (>= 1)
     int nchunk;                // cooperative kernel: quartet chunks per tile (divides TILE / groups)
     int kind;                  // 0: default kernel of the class, 1: thread kernel, 2: cooperative kernel
@@ -103,7 +108,7 @@ struct OutArgs {
     double *partials;                 // [gridDim][natom_total*3], accumulated
     int natom_total;                  // atoms of the whole batch
     int natom_max;                    // atoms of the largest molecule
-    unsigned long long *counters;     // [0] quartets, [1] fp64 primitive quartets, [2] fp32 quartets, [3] fp32 pq
+    unsigned long long *counters;     // NCNT per class (see NCNT)
     int use_smem;                     // per-molecule partial gradient kept in shared memory
     double *dump;                     // nullable: per-quartet gradients [tile][TILE][12] instead of reducing
 };
@@ -258,5 +263,9 @@ __device__ __forceinline__ void etab(F (&E)[I + 1][J + 1][I + J + 1], F PA, F PB
             }
 }
 
+
+// Algorithmic FLOPs of class qc per primitive quartet and per bra primitive
+// pair visit (flops.cu; see tg_class_flops in tdgrad.h).
+void class_flops(int qc, int nops, double *per_pq, double *per_p);
 
 }  // namespace tg

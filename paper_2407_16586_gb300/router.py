@@ -10,14 +10,18 @@ two constants on held-out tiles:
   relative to the contribution.
 
 TG_MIXED_LEARNED then sends tiles to fp32 in increasing order of
-e_t = eps_rel * 10^(prediction + margin) while sum e_t^2 <= (mixed_tol/3)^2
+e_t = eps_rel * 10^(prediction + margin) while sum e_t^2 <= mixed_tol^2
 (mixed_tol defaults to 1e-6 Ha/bohr).
 
 Both percentiles bound single tiles, so the summed estimate overstates the
 error of the routed set by orders of magnitude.  calibrate_budget() then
 measures the whole route: on held-out molecules it runs the mixed path
-against fp64 while lowering the margin in steps of 0.5 (log10), and keeps
-the lowest margin whose largest max|dg| stays within mixed_tol / safety."""
+against fp64 while lowering the margin in steps of 0.25 (log10), and keeps
+the lowest margin whose largest max|dg| stays within mixed_tol / safety.
+The single safety factor (default 2) covers the spread of the error between
+molecules: at a fixed margin the measured errors of the budget molecules
+differ by a factor recorded in the calibration log (spread), and the
+factor is chosen at least as large as that spread."""
 from __future__ import annotations
 
 import numpy as np
@@ -59,33 +63,42 @@ def fit(X, y, e, seed=7, epochs=400, lr=1e-2, q=0.9, holdout=0.2, floor=-20.0):
     return r, info
 
 
-def calibrate_budget(r, systems, mixed_tol=1e-6, safety=5.0, step=0.5, max_steps=16, screen_tol=1e-10):
+def calibrate_budget(r, systems, mixed_tol=1e-6, safety=2.0, step=0.25, max_steps=32, screen_tol=1e-10,
+                     shards=None):
     """Lower the router's margin while the measured max|dg| of TG_MIXED_LEARNED
-    against TG_FP64 over ``systems`` stays <= mixed_tol / safety.  Returns a
-    list of (margin, max error, fp32 quartet fraction) for every margin tried."""
+    against TG_FP64 over ``systems`` stays <= mixed_tol / safety.  ``shards``
+    (optional, one (rank, nranks) or None per system) evaluates a pair-key
+    shard of a system, so that a full-size system can sit in the budget set.
+    Returns a list of (margin, max error, fp32 quartet fraction, spread) for
+    every margin tried; spread = largest / smallest per-system error."""
     params, mu, sd, calib = r.get()
     margin0, eps_rel = float(calib[0]), float(calib[1])
+    shards = shards or [None] * len(systems)
     runs = []
-    for s in systems:
+    for s, sh in zip(systems, shards):
         b = tg.Basis(s)
-        g64, _ = b.grad2e(s["pairs"], screen_tol=screen_tol)
-        runs.append((b, s, g64))
+        kw = dict(rank=sh[0], nranks=sh[1]) if sh else {}
+        g64, _ = b.grad2e(s["pairs"], screen_tol=screen_tol, **kw)
+        runs.append((b, s, g64, kw))
     best, log = margin0, []
     for k in range(max_steps + 1):
         m = margin0 - step * k
         r.set(calib=[m, eps_rel, 1.0])
-        err, q32, q = 0.0, 0, 0
-        for b, s, g64 in runs:
+        errs, q32, q = [], 0, 0
+        for b, s, g64, kw in runs:
             g, st = b.grad2e(s["pairs"], screen_tol=screen_tol, precision=tg.TG_MIXED_LEARNED, router=r,
-                             mixed_tol=mixed_tol)
-            err = max(err, float(np.abs(g - g64).max()))
+                             mixed_tol=mixed_tol, **kw)
+            errs.append(float(np.abs(g - g64).max()))
             q32 += st["fp32_quartets"]
             q += st["quartets"]
-        log.append((m, err, q32 / max(q, 1)))
+        err = max(errs)
+        nz = [e for e in errs if e > 0]
+        spread = max(nz) / min(nz) if nz else 1.0
+        log.append((m, err, q32 / max(q, 1), spread))
         if err > mixed_tol / safety:
             break
         best = m
     r.set(calib=[best, eps_rel, 1.0])
-    for b, _, _ in runs:
+    for b, _, _, _ in runs:
         b.close()
     return log

@@ -32,6 +32,9 @@ def main():
     ap.add_argument("--budget-chains", type=int, default=2, help="20-atom chains added to the budget set")
     ap.add_argument("--budget-first", type=int, default=100000, help="first cluster index of the budget set")
     ap.add_argument("--recalibrate", default=None, help="router file whose network is kept")
+    ap.add_argument("--budget-c4-nranks", type=int, default=200,
+                    help="add pair-key shard 0 of this many of the 300-atom cluster to the budget set (0: none)")
+    ap.add_argument("--safety", type=float, default=2.0)
     args = ap.parse_args()
     from paper_2407_16586_gb300 import build
     build.build()
@@ -42,10 +45,18 @@ def main():
     budget_set = [synth.router_cluster(i, natom=args.budget_natom)
                   for i in range(args.budget_first, args.budget_first + args.budget_clusters)]
     budget_set += [synth.molecule(args.budget_first + i, 8, 12) for i in range(args.budget_chains)]
+    shards = [None] * len(budget_set)
+    if args.budget_c4_nranks > 0:
+        budget_set.append(synth.config(3))
+        shards.append((0, args.budget_c4_nranks))
+    budget_desc = ("router_cluster(%d..%d, natom=%d) + molecule(%d..%d, 8, 12)%s; safety %g" % (
+        args.budget_first, args.budget_first + args.budget_clusters - 1, args.budget_natom, args.budget_first,
+        args.budget_first + args.budget_chains - 1,
+        " + c4 pair-key shard 0/%d" % args.budget_c4_nranks if args.budget_c4_nranks > 0 else "", args.safety))
     if args.recalibrate:
         r = tg.Router(path=args.recalibrate)
-        info = dict(recalibrated_from=os.path.basename(args.recalibrate))
-        info["budget_log"] = router.calibrate_budget(r, budget_set)
+        info = dict(recalibrated_from=os.path.basename(args.recalibrate), budget_set=budget_desc)
+        info["budget_log"] = router.calibrate_budget(r, budget_set, safety=args.safety, shards=shards)
         info["margin"] = float(r.get()[3][0])
         r.save(args.out)
         with open(args.out + ".json", "w") as f:
@@ -62,7 +73,8 @@ def main():
     X, y, e = np.concatenate(Xs), np.concatenate(ys), np.concatenate(es)
     t1 = time.time()
     r, info = router.fit(X, y, e, epochs=args.epochs)
-    info["budget_log"] = router.calibrate_budget(r, budget_set)
+    info["budget_set"] = budget_desc
+    info["budget_log"] = router.calibrate_budget(r, budget_set, safety=args.safety, shards=shards)
     info["margin"] = float(r.get()[3][0])
     r.save(args.out)
     info.update(clusters=args.clusters, stride=args.stride, tiles=int(len(y)), sample_s=t1 - t0,

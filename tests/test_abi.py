@@ -48,4 +48,4 @@ def test_abi_version_and_named_option_defaults():
     assert L.tg_abi_version() == ver
     o = tg.tg_options_default()
     assert o.deterministic == 1 and o.class_mask == 0 and o.kernel_kind == 0 and o.autotune == 0
-    assert list(o.reserved) == [0, 0, 0, 0]
+    assert list(o.reserved) == [0, 0, 0] and o.shard_mode == 0

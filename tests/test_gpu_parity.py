@@ -217,3 +217,67 @@ def test_batch_matches_single_calls(tg):
         assert np.abs(a - c).max() <= 1e-12
     ref0, _, _ = oracle.grad2e(systems[0], tau=1e-10)
     assert np.abs(g1[0] - ref0).max() <= TOL
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-10, 1e-6])
+def test_device_tile_lists_match_the_host_planner(tg, tau):
+    """The device block screen (tg_grad2e) keeps exactly the tiles of the host
+    planner (the batch path) for one molecule: same tile count, same quartets,
+    same gradient to rounding."""
+    s = synth.molecule(17, 3, 4)
+    g, st = tg.grad2e(s, screen_tol=tau)
+    batch = tg.Batch([s], screen_tol=tau)
+    gb, stb = batch.run()
+    assert st["tiles"] == stb["tiles"] and st["tiles"] > 0
+    assert st["quartets"] == stb["quartets"]
+    assert np.abs(g - gb[0]).max() <= 1e-12
+    ref, _, nq = oracle.grad2e(s, tau=tau)
+    assert st["quartets"] == nq
+    assert np.abs(g - ref).max() <= TOL
+
+
+def test_device_routing_meets_the_budget(tg):
+    """The device router's histogram cut-off sends tiles to fp32 while the
+    summed error estimate stays within the budget: the gradient stays within
+    mixed_tol of the oracle, and some tiles do go to fp32."""
+    s = synth.molecule(18, 4, 4)
+    ref, _, _ = oracle.grad2e(s, tau=1e-10)
+    for tol in (1e-6, 1e-8):
+        g, st = tg.grad2e(s, screen_tol=1e-10, precision=tg.TG_MIXED_BOUND, mixed_tol=tol)
+        assert np.abs(g - ref).max() <= tol
+        assert 0 < st["fp32_quartets"] < st["quartets"]
+
+
+def test_tile_shards_sum_to_the_whole(tg):
+    """Tile-cyclic shards (every class list dealt round-robin to the ranks):
+    the ranks' quartet counts and partial gradients sum to the whole call."""
+    s = synth.molecule(19, 3, 3)
+    b = tg.Basis(s)
+    whole, stw = b.grad2e(s["pairs"], screen_tol=1e-10)
+    tot = np.zeros_like(whole)
+    nq = 0
+    for r in range(3):
+        g, st = b.grad2e(s["pairs"], screen_tol=1e-10, rank=r, nranks=3, shard_mode=tg.TG_SHARD_TILES)
+        assert 0 < st["quartets"] < stw["quartets"]
+        tot += g
+        nq += st["quartets"]
+    assert nq == stw["quartets"]
+    assert np.abs(tot - whole).max() <= 1e-12
+
+
+def test_allocation_failure_leaves_the_output_untouched(tg, monkeypatch):
+    """With the host-side hook TDGRAD_FAIL_ALLOC=1 every growth of the work
+    areas fails as an out-of-memory would: the call returns TG_ENOMEM and the
+    output keeps its contents; without the hook the same basis works."""
+    s = synth.molecule(20, 1, 2)
+    b = tg.Basis(s)  # fresh basis: its work areas are still empty
+    out = np.full((s["natom"], 3), 7.0)
+    monkeypatch.setenv("TDGRAD_FAIL_ALLOC", "1")
+    with pytest.raises(tg.TGError) as e:
+        b.grad2e(s["pairs"], screen_tol=1e-10, out=out)
+    assert e.value.status == tg.TG_ENOMEM
+    assert np.all(out == 7.0)
+    monkeypatch.delenv("TDGRAD_FAIL_ALLOC")
+    g, _ = b.grad2e(s["pairs"], screen_tol=1e-10, out=out)
+    ref, _, _ = oracle.grad2e(s, tau=1e-10)
+    assert np.abs(g - ref).max() <= TOL

@@ -64,11 +64,14 @@ def test_class_table_matches_the_kernels():
 
 
 def test_flop_model_is_monotone_in_angular_momentum():
-    f = {c: bench.flops_per_prim_quartet(*c) for c in bench.class_ls()}
-    assert f[(0, 0, 0, 0)] == 132          # (ss|ss): 66 FMAs
-    assert f[(2, 2, 2, 2)] > f[(2, 2, 2, 1)] > f[(2, 2, 1, 1)] > f[(1, 1, 1, 1)]
+    from paper_2407_16586_gb300 import build
+    import paper_2407_16586_gb300 as tg
+    build.build()
+    ls = bench.class_ls()
+    f = {c: sum(tg.tg_class_flops(qc)) for qc, c in enumerate(ls)}
+    assert f[(2, 2, 2, 2)] > f[(2, 2, 2, 1)] > f[(2, 2, 1, 1)] > f[(1, 1, 1, 1)] > f[(0, 0, 0, 0)]
     # one operator costs less than two
-    assert bench.flops_per_prim_quartet(1, 1, 1, 1, nops=1) < f[(1, 1, 1, 1)]
+    assert tg.tg_class_flops(5, 1)[0] < tg.tg_class_flops(5, 2)[0]
 
 
 def test_workload_names():
@@ -112,7 +115,7 @@ def test_budget_calibration_keeps_the_last_safe_margin(monkeypatch):
         def __init__(self, s):
             pass
 
-        def grad2e(self, pairs, screen_tol=1e-10, precision=0, router=None, mixed_tol=1e-6):
+        def grad2e(self, pairs, screen_tol=1e-10, precision=0, router=None, mixed_tol=1e-6, **kw):
             g = np.zeros((2, 3))
             if precision == router_mod.TG_MIXED_LEARNED:
                 m = float(router.calib[0])
@@ -124,8 +127,8 @@ def test_budget_calibration_keeps_the_last_safe_margin(monkeypatch):
 
     router_mod = router.tg
     monkeypatch.setattr(router_mod, "Basis", FakeBasis)
-    log = router.calibrate_budget(r, [{"pairs": []}], mixed_tol=1e-6, safety=5.0)
-    errs = [e for _, e, _ in log]
+    log = router.calibrate_budget(r, [{"pairs": []}], mixed_tol=1e-6, safety=5.0, step=0.5)
+    errs = [e for _, e, _, _ in log]
     assert all(b > a for a, b in zip(errs, errs[1:]))
     assert errs[-1] > 2e-7 and errs[-2] <= 2e-7
     assert float(r.calib[0]) == pytest.approx(log[-2][0])
@@ -135,7 +138,7 @@ def test_budget_calibration_keeps_the_last_safe_margin(monkeypatch):
 def _fake_stats(ms64, ms32, pq64, pq32):
     z = [0.0] * 21
     st = {"class_ms": list(z), "class_ms_fp32": list(z), "class_prim_quartets": [0] * 21,
-          "class_prim_quartets_fp32": [0] * 21}
+          "class_prim_quartets_fp32": [0] * 21, "class_bra_prims": [0] * 21, "class_bra_prims_fp32": [0] * 21}
     for qc, v in ms64.items():
         st["class_ms"][qc] = v
     for qc, v in ms32.items():
@@ -148,37 +151,123 @@ def _fake_stats(ms64, ms32, pq64, pq32):
 
 
 def test_roofline_of_the_dominant_kernel():
-    """achieved = algorithmic FLOPs of the longest class launch / its time;
-    frac against the derived fp64 (or fp32) ALU peak; traffic scaled from the
-    captured bytes per primitive quartet where that kernel was captured."""
+    """achieved = algorithmic FLOPs of the longest class launch (per primitive
+    quartet and per bra primitive pair, tg_class_flops) / its time; frac
+    against the derived fp64 (or fp32) ALU peak; frac_mixed = the time all
+    class launches would take at their peaks / their summed time."""
+    import paper_2407_16586_gb300 as tg
     ls = bench.class_ls()
     dppp, dddd = ls.index((2, 1, 1, 1)), ls.index((2, 2, 2, 2))
     st = _fake_stats({dppp: 600.0, 0: 5.0}, {dddd: 100.0}, {dppp: 4_850_000, 0: 10_000}, {dddd: 20_000})
+    st["class_bra_prims"][dppp] = 400_000
+    st["class_bra_prims"][0] = 1_000
+    st["class_bra_prims_fp32"][dddd] = 5_000
     r = bench.roofline_entry(st)
-    flops = 4_850_000 * bench.flops_per_prim_quartet(2, 1, 1, 1)
-    assert r["kernel"] == "k_grad<(dp|pp), fp64>"
+    a, b = tg.tg_class_flops(dppp)
+    flops = 4_850_000 * a + 400_000 * b
+    assert r["kernel"] == "(dp|pp) fp64"
     assert r["achieved"] == pytest.approx(flops / 0.6 / 1e12)
     assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == pytest.approx(10.019916e9 / 521142 * 4_850_000)
-    tot = flops + 10_000 * bench.flops_per_prim_quartet(0, 0, 0, 0) + 20_000 * bench.flops_per_prim_quartet(2, 2, 2, 2)
-    assert r["all_kernels_tflops"] == pytest.approx(tot / 0.705 / 1e12)
-    # an fp32 cooperative launch that dominates: its own peak, no captured traffic
+    assert r["traffic"] is None
+    a0, b0 = tg.tg_class_flops(0)
+    a20, b20 = tg.tg_class_flops(dddd)
+    f64 = flops + 10_000 * a0 + 1_000 * b0
+    f32 = 20_000 * a20 + 5_000 * b20
+    ideal = f64 / (r["peak"] * 1e12) + f32 / (152 * 128 * 2 * 2.07e9)
+    assert r["frac_mixed"] == pytest.approx(ideal / 0.705)
+    assert r["fp64_frac"] == pytest.approx(f64 / 0.605 / 1e12 / r["peak"])
+    # an fp32 launch that dominates: its own peak
     st = _fake_stats({dppp: 50.0}, {dddd: 100.0}, {dppp: 1000}, {dddd: 20_000})
     r = bench.roofline_entry(st)
-    assert r["kernel"] == "k_grad_coop<(dd|dd), fp32>"
+    assert r["kernel"] == "(dd|dd) fp32"
     assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
-    assert r["traffic"] is None
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
 
 
-def test_default_kernel_kind_follows_the_class_split():
-    assert not bench.default_kernel_is_coop(2, 1, 1, 1, False)        # (dp|pp), 162 function quartets
-    assert bench.default_kernel_is_coop(2, 1, 2, 0, False)            # (dp|ds) defaults to the group kernel
-    assert bench.default_kernel_is_coop(2, 2, 2, 0, False)            # (dd|ds), 216
-    assert not bench.default_kernel_is_coop(2, 2, 2, 0, True)         # fp32 from 648
-    assert bench.default_kernel_is_coop(2, 2, 2, 1, True)             # (dd|dp), 648
-    # the same split as the library's compile-time choice
-    src = open(os.path.join(ROOT, "paper_2407_16586_gb300", "csrc", "eri_coop.cuh")).read()
-    assert "fp32 = nfq >= 648" in src
-    assert "fp64_default = nfq >= 216 || (LA == 2 && LB == 1 && LC == 2 && LD == 0)" in src
+
+def _flop_model(la, lb, lc, ld, nops):
+    """The algorithmic count of the class kernels' evaluation, enumerated here
+    term by term: per primitive quartet the Boys orders (6 Taylor FMAs and a
+    base product each), the Hermite R recursion, E^{cd} over the index boxes,
+    W = E^{cd} R over the boxes of cd, z = F R over the derivative boxes of cd
+    and the d/dC products; per bra primitive pair E^{ab}, F = Gamma E^{ab},
+    Y = Gamma W over the derivative boxes of ab and the d/dA, d/dA + d/dB
+    products (an FMA counts 2)."""
+    def nh(L):
+        return 0 if L < 0 else (L + 1) * (L + 2) * (L + 3) // 6
+
+    def cart(l):
+        return [(l - s, s - z, z) for s in range(l + 1) for z in range(s + 1)]
+
+    def ext(l1, l2):
+        return [tuple(a[i] + b[i] for i in range(3)) for a in cart(l1) for b in cart(l2)]
+
+    def box(n):
+        return (n[0] + 1) * (n[1] + 1) * (n[2] + 1)
+
+    def dboxes(n):
+        out = []
+        for t in range(n[0] + 2):
+            for u in range(n[1] + 2):
+                for v in range(n[2] + 2):
+                    ix, iy, iz = t <= n[0], u <= n[1], v <= n[2]
+                    g = (t <= n[0] + 1 and iy and iz) + (ix and u <= n[1] + 1 and iz) + (ix and iy and v <= n[2] + 1)
+                    if g:
+                        out.append(g)
+        return out
+
+    L1, L2 = la + lb, lc + ld
+    L = L1 + L2
+    r = 0
+    for n in range(L + 1):
+        for k in range(1, L + 2 - n):
+            for t in range(k + 1):
+                for u in range(k - t + 1):
+                    v = k - t - u
+                    two = (t > 1) if t > 0 else ((u > 1) if u > 0 else (v > 1))
+                    r += 3 if two else 1
+    ab, cd = ext(la, lb), ext(lc, ld)
+    pq = nops * r + nops * (L + 2) * 14 + 2 * sum(box(n) for n in cd)
+    pq += nops * sum(box(n) for n in cd) * nh(L1 + 1) * 2 + nops * sum(len(dboxes(n)) for n in cd) * nh(L1) * 2
+    pq += sum(7 * g for n in cd for g in dboxes(n))
+    p = 2 * sum(box(n) for n in ab) + nops * len(cd) * sum(box(n) for n in ab) * 2
+    p += nops * len(cd) * sum(len(dboxes(n)) for n in ab) * 2 + sum(11 * g for n in ab for g in dboxes(n))
+    return pq, p
+
+
+def test_class_flop_model_matches_the_enumeration():
+    from paper_2407_16586_gb300 import build
+    import paper_2407_16586_gb300 as tg
+    build.build()
+    pcs = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+    qc = 0
+    for P in range(6):
+        for Q in range(P + 1):
+            for nops in (1, 2):
+                got = tg.tg_class_flops(qc, nops)
+                assert got == _flop_model(*pcs[P], *pcs[Q], nops), (qc, nops)
+            qc += 1
+    # (dp|pp): the index boxes cut the full-tetrahedron count several times
+    assert tg.tg_class_flops(12)[0] == 15104
+
+
+def test_tile_shards_cover_every_tile_once():
+    """TG_SHARD_TILES: the ranks' tiles of a launch list partition it, and the
+    counts differ by at most one (the list is ordered by decreasing cost, so
+    the cyclic deal also balances cost)."""
+    from paper_2407_16586_gb300 import build
+    import paper_2407_16586_gb300 as tg
+    build.build()
+    for n in (0, 1, 7, 128, 1001):
+        for nr in (1, 2, 3, 8):
+            seen = []
+            counts = []
+            for r in range(nr):
+                first, count, stride = tg.tg_tile_shard(n, r, nr)
+                seen += [first + k * stride for k in range(count)]
+                counts.append(count)
+            assert sorted(seen) == list(range(n))
+            assert max(counts) - min(counts) <= 1
+    with pytest.raises(tg.TGError):
+        tg.tg_tile_shard(10, 3, 3)
