@@ -251,6 +251,133 @@ def cpu_baseline(s, name, shards=600, shard=0):
             "sample": "shard %d of %d of the %s quartets (%d quartets, %.1f s)" % (shard, shards, name, nq, dt)}
 
 
+def c3_systems(name):
+    """"c3" = the 64 molecules of 20-120 atoms; "c3:N" = the N smallest of them."""
+    from paper_2407_16586_gb300 import synth
+    ms = synth.config(2)
+    if name == "c3":
+        return ms, "c3: 64 molecules of 21-117 atoms (4837 atoms), c2 recipe, batched"
+    n = int(name.split(":")[1])
+    ms = sorted(ms, key=lambda m: m["natom"])[:n]
+    return ms, "c3:%d: the %d smallest c3 molecules (%d-%d atoms, %d atoms), c2 recipe, batched" % (
+        n, n, ms[0]["natom"], ms[-1]["natom"], sum(m["natom"] for m in ms))
+
+
+def run_c3(args, prec, router, torch):
+    """Batched uneven molecules: one planned batch (tg_batch_*: per-class
+    launches over all molecules, replayed from a captured CUDA graph, the
+    kernel form and grid of every class list autotuned) against single
+    tg_grad2e calls on the same molecules (host buffers: the end-to-end
+    figure)."""
+    import numpy as np
+    import paper_2407_16586_gb300 as tg
+    systems, wname = c3_systems(args.workload)
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    t = time.perf_counter()
+    batch = tg.Batch(systems, screen_tol=TAU, precision=prec, router=router, autotune=True)
+    create_s = time.perf_counter() - t
+    for _ in range(args.warmup):
+        gb, st0 = batch.run()
+    ms_b, q = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        gb, st = batch.run()
+        ms_b.append(1e3 * (time.perf_counter() - t))
+        q += st["quartets"]
+    bases = [tg.Basis(m) for m in systems]
+    for b, m in zip(bases, systems):
+        b.grad2e(m["pairs"], screen_tol=TAU, precision=prec, router=router)
+    ms_s, qs, err = [], 0, 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        outs = []
+        for b, m in zip(bases, systems):
+            g, st1 = b.grad2e(m["pairs"], screen_tol=TAU, precision=prec, router=router)
+            outs.append(g)
+            qs += st1["quartets"]
+        ms_s.append(1e3 * (time.perf_counter() - t))
+    err = max(float(np.abs(a - c).max()) for a, c in zip(gb, outs))
+    msb = sum(ms_b) / len(ms_b)
+    line = {"metric": METRIC, "value": q / (sum(ms_b) / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": msb, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64", "data": "synthetic",
+            "config": {"workload": wname, "precision": args.precision, "screen_tol": TAU, "molecules": len(systems),
+                       "quartets_per_step": st0["quartets"], "fp32_quartets_per_step": st0["fp32_quartets"],
+                       "l2": "flushed (512 MB write) before each timed step",
+                       "batch": "one tg_batch: plan + autotune + graph capture at creation, graph replay per step",
+                       "batch_create_s": create_s},
+            "e2e": {"value": qs / (sum(ms_s) / 1e3), "unit": UNIT, "h2d_bytes_per_step":
+                    sum(a.nbytes + b_.nbytes for m in systems for (a, b_, *_r) in m["pairs"]),
+                    "d2h_bytes_per_step": sum(m["natom"] * 24 for m in systems),
+                    "how": "one tg_grad2e call per molecule, host densities"},
+            "single_calls_ms_per_step": sum(ms_s) / len(ms_s), "batch_vs_single_max_abs_dg": err,
+            "gpu_launches": st0["launches"]}
+    print(json.dumps(line))
+    return 0
+
+
+def run_large(args, prec, router, torch):
+    """The 300-atom c4 cluster: one step takes minutes, so the kernels are
+    warmed on c1, then ONE mixed step and ONE fp64 step are timed (CUDA events
+    on the launching stream, per-class events on), and the fp64 gradient is
+    the reference of the mixed one.  No end-to-end repeat (the host copies
+    are 0.2 GB against minutes of kernels)."""
+    import numpy as np
+    import paper_2407_16586_gb300 as tg
+    from paper_2407_16586_gb300 import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    c1 = synth.config(0)
+    b1 = tg.Basis(c1)
+    for _ in range(2):
+        b1.grad2e(c1["pairs"], screen_tol=TAU, precision=prec, router=router)
+    s, wname = workload(args.workload)
+    basis = tg.Basis(s)
+    dpairs = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev), cj, ck, cl, om)
+              for (a, b, cj, ck, cl, om) in s["pairs"]]
+    gout = torch.empty((s["natom"], 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one(precision):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), st, gout.cpu().numpy().copy()
+
+    rows, stop = [], threading.Event()
+    th = threading.Thread(target=_clock_sampler, args=(stop, rows), daemon=True)
+    th.start()
+    time.sleep(0.3)
+    ms, st, g = one(prec)
+    ms64, st64, g64 = (ms, st, g) if prec == tg.TG_FP64 else one(tg.TG_FP64)
+    stop.set()
+    th.join(timeout=2)
+    line = {"metric": METRIC, "value": st["quartets"] / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64", "data": "synthetic",
+            "config": {"workload": wname, "precision": args.precision, "screen_tol": TAU, "mixed_tol": 1e-6,
+                       "quartets_per_step": st["quartets"], "fp32_quartets_per_step": st["fp32_quartets"],
+                       "prim_quartets_per_step": st["prim_quartets"], "pairs": st["pairs"], "tiles": st["tiles"],
+                       "warm-up": "two c1 calls (kernels and context loaded); one timed step per precision",
+                       "l2": "flushed (512 MB write) before each timed step"},
+            "e2e": None, "gpu_launches": st["launches"], "plan_ms": st["plan_ms"],
+            "roofline": roofline_entry(st), "clocks": _clocks_summary(rows, 0),
+            "fp64": {"ms_per_step": ms64, "value": st64["quartets"] / (ms64 / 1e3),
+                     "max_abs_dg_vs_fp64": float(np.abs(g - g64).max()), "speedup_vs_fp64": ms64 / ms,
+                     "roofline": roofline_entry(st64), "plan_ms": st64["plan_ms"]}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,7 +389,7 @@ def main():
     ap.add_argument("--router", default=os.path.join(ROOT, "paper_2407_16586_gb300", "data", "router.bin"))
     ap.add_argument("--ref-shards", type=int, default=None, help="oracle shards (default 600; 50000 for c4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", help='c2 (default), c1, c4, or chain:SEED:NHEAVY:NH')
+    ap.add_argument("--workload", default="c2", help='c2 (default), c1, c3, c3:N, c4, or chain:SEED:NHEAVY:NH')
     ap.add_argument("--bound-steps", type=int, default=1, help="timed mixed-bound steps for the comparison (0: skip)")
     ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
     args = ap.parse_args()
@@ -298,6 +425,10 @@ def main():
             "fp32": tg.TG_FP32}[args.precision]
     router = tg.Router(path=args.router) if prec == tg.TG_MIXED_LEARNED else None
 
+    if args.workload.startswith("c3"):
+        return run_c3(args, prec, router, torch)
+    if args.workload == "c4":
+        return run_large(args, prec, router, torch)
     s, wname = workload(args.workload)
     basis = tg.Basis(s)
     dev = torch.device("cuda", local)

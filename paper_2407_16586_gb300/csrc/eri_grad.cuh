@@ -397,9 +397,11 @@ __device__ void quartet_fp64(const GeoArgs &geo, const DensArgs &den, const Prim
     }
 }
 
-// fp32 Boys function F_m(T), m = 0..M: fp32 Taylor table and downward
-// recursion for T >= 1; below T = 1 the fp64 routine is used.  Relative
-// accuracy ~1e-7.
+// Boys function F_m(T), m = 0..M, for the fp32 route.  Below T = 1 the whole
+// fp64 routine runs; for 1 <= T < 36 the top order comes from a Taylor step of
+// the fp32 table and the downward recursion F_m = (2T F_{m+1} + e^-T)/(2m+1)
+// runs in fp64 (with e^-T in fp64); for T >= 36 the upward recursion is
+// stable and runs in fp32.  Relative accuracy ~1e-7 (the fp32 seed).
 template <int M>
 __device__ __forceinline__ void boys_mixed(float T, float (&F)[M + 1], const double *__restrict__ tab)
 {
@@ -419,10 +421,15 @@ __device__ __forceinline__ void boys_mixed(float T, float (&F)[M + 1], const dou
 #pragma unroll
         for (int k = BOYS_TAYLOR - 1; k >= 0; --k) acc = row[k] + acc * d * (1.0f / (k + 1));
         F[M] = acc;
-        const float et = __expf(-T);
-        const float t2 = 2.0f * T;
+        const double Td = (double)T;
+        const double et = exp(-Td);
+        const double t2 = 2.0 * Td;
+        double f = (double)acc;
 #pragma unroll
-        for (int m = M - 1; m >= 0; --m) F[m] = (t2 * F[m + 1] + et) * (1.0f / (2 * m + 1));
+        for (int m = M - 1; m >= 0; --m) {
+            f = (t2 * f + et) * (1.0 / (2 * m + 1));
+            F[m] = (float)f;
+        }
     } else {
         const float it = 1.0f / T;
         F[0] = 0.88622692545275801365f * sqrtf(it);
@@ -517,7 +524,8 @@ __device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const Pri
                 }
         }
 
-        float fA[3] = {0.f, 0.f, 0.f}, fC[3] = {0.f, 0.f, 0.f}, fT[3] = {0.f, 0.f, 0.f};
+        // every primitive quartet's contribution is added in fp64
+        double fA[3] = {0.0, 0.0, 0.0}, fC[3] = {0.0, 0.0, 0.0}, fT[3] = {0.0, 0.0, 0.0};
         for (int jk = 0; jk < nkp; ++jk) {
             const int kp = pk0 + jk;
             const float qf = pp.fp[kp], Kcd = pp.fK[kp];
@@ -560,6 +568,8 @@ __device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const Pri
                             E3k[cd][hidx(t, u, v)] = kx[t] * ky[u] * kz[v] * w;
                         }
             }
+            // this primitive quartet's contribution, formed in fp32, added to fp64 below
+            float qA[3] = {0.f, 0.f, 0.f}, qC[3] = {0.f, 0.f, 0.f}, qT[3] = {0.f, 0.f, 0.f};
             for (int o = 0; o < nops; ++o) {
                 float R[NR];
                 {
@@ -647,12 +657,12 @@ __device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const Pri
                         q1 += ex[t] * vy;
                         q2 += ex[t] * vz;
                     }
-                    fA[0] += a0;
-                    fA[1] += a1;
-                    fA[2] += a2;
-                    fT[0] += q0;
-                    fT[1] += q1;
-                    fT[2] += q2;
+                    qA[0] += a0;
+                    qA[1] += a1;
+                    qA[2] += a2;
+                    qT[0] += q0;
+                    qT[1] += q1;
+                    qT[2] += q2;
                 }
                 // ---- ket side: z^{cd} (registers), then d/dC
                 for (int cd = 0; cd < NCD; ++cd) {
@@ -710,17 +720,23 @@ __device__ void quartet_fp32r(const GeoArgs &geo, const DensArgs &den, const Pri
                         c1 += kx[t] * uy;
                         c2 += kx[t] * uz;
                     }
-                    fC[0] += c0;
-                    fC[1] += c1;
-                    fC[2] += c2;
+                    qC[0] += c0;
+                    qC[1] += c1;
+                    qC[2] += c2;
                 }
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                fA[i] += (double)qA[i];
+                fC[i] += (double)qC[i];
+                fT[i] += (double)qT[i];
             }
         }
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            gA[i] += (double)fA[i];
-            gC[i] += (double)fC[i];
-            gT[i] += (double)fT[i];
+            gA[i] += fA[i];
+            gC[i] += fC[i];
+            gT[i] += fT[i];
         }
     }
 #pragma unroll
