@@ -51,6 +51,9 @@ def _configure(lib):
         ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
         ctypes.c_int, _dp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.or_grad2e.restype = ctypes.c_int
+    lib.or_fock2e.argtypes = basis_args + [
+        ctypes.c_int, ctypes.POINTER(_dp), _dp, _dp, _dp, _dp, ctypes.c_int, _dp]
+    lib.or_fock2e.restype = ctypes.c_int
     return lib
 
 
@@ -164,3 +167,24 @@ def grad2e(s, pairs=None, mode="canonical", tau=0.0, rank=0, nranks=1, nthreads=
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     return grad, (e.value if want_energy else None), nq.value
+
+
+def fock2e(s, pairs=None, nthreads=0):
+    """Fock-type matrix (nbf x nbf) of the pair list [(B, c_J, c_K, c_K_lr, omega)]:
+    F[mu nu] = sum_p sum_{lam sig} B[lam sig] (c_J (mu nu|lam sig) + c_K (mu lam|nu sig)
+    + c_K_lr (mu lam|nu sig)_omega), the two-electron part of eqs. G_2e and zfock
+    (Sec. II.B).  Plain definition over all ordered shell quartets."""
+    bs = _Basis(s)
+    npair = len(pairs)
+    mats = [np.ascontiguousarray(p[0], dtype=np.float64) for p in pairs]
+    nbf = mats[0].shape[0]
+    Bp = (_dp * max(npair, 1))(*[_d(m) for m in mats])
+    cJ = np.array([p[1] for p in pairs] + [0.0])
+    cK = np.array([p[2] for p in pairs] + [0.0])
+    cKlr = np.array([p[3] for p in pairs] + [0.0])
+    om = np.array([p[4] for p in pairs] + [0.0])
+    F = np.zeros((nbf, nbf))
+    rc = _load().or_fock2e(*bs.args(), npair, Bp, _d(cJ), _d(cK), _d(cKlr), _d(om), int(nthreads), _d(F))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return F

@@ -924,3 +924,98 @@ int or_grad2e(int natom, const double *xyz, int nshell, const int *sh_atom, cons
     basis_free(&bs);
     return 0;
 }
+
+/*
+ * Fock-type matrices of a list of density matrices (Sec. II.B, the
+ * two-electron part of eqs. G_2e and zfock; the XC kernel term is not part
+ * of it):
+ *   F[mu nu] = sum_p sum_{lam sig} B_p[lam sig] ( c_J (mu nu|lam sig)
+ *              + c_K (mu lam|nu sig) + c_K_lr (mu lam|nu sig)_w ),
+ * one nbf x nbf matrix F (overwritten), row-major.  Plain definition: every
+ * ordered shell quartet (a b|c d) is evaluated once; its integrals
+ * (m n|l s), m in a, n in b, l in c, s in d, enter the Coulomb block
+ * F[m][n] with B[l][s] and the exchange block F[m][l] with B[n][s].  No
+ * screening.  Returns 0, or -1 on bad arguments.
+ */
+int or_fock2e(int natom, const double *xyz, int nshell, const int *sh_atom, const int *sh_l,
+              const int *sh_nprim, const double *exps, const double *coefs,
+              int npair, const double *const *Bm, const double *cJ, const double *cK,
+              const double *cKlr, const double *omega, int nthreads, double *F)
+{
+    init_tri();
+    if (natom < 1 || nshell < 1 || npair < 0 || !F) return -1;
+    for (int s = 0; s < nshell; ++s) if (sh_l[s] < 0 || sh_l[s] > OR_MAXL || sh_nprim[s] < 1) return -1;
+    obasis bs;
+    basis_setup(&bs, natom, xyz, nshell, sh_atom, sh_l, sh_nprim, exps, coefs);
+    int use_lr = 0;
+    double om = 0.0;
+    for (int p = 0; p < npair; ++p)
+        if (cKlr[p] != 0.0 && omega[p] > 0) {
+            if (use_lr && omega[p] != om) { basis_free(&bs); return -1; }
+            use_lr = 1;
+            om = omega[p];
+        }
+    const int nbf = bs.nbf, ns = nshell, nops = use_lr ? 2 : 1;
+    const double omegas[2] = {0.0, om};
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    int nth = omp_get_max_threads();
+#else
+    int nth = 1;
+    (void)nthreads;
+#endif
+    double *acc = (double *)calloc((size_t)nth * nbf * nbf, sizeof(double));
+#pragma omp parallel
+    {
+#ifdef _OPENMP
+        int t = omp_get_thread_num();
+#else
+        int t = 0;
+#endif
+        double *Ft = acc + (size_t)t * nbf * nbf;
+        quartet_ws q;
+        ws_alloc(&q);
+#pragma omp for schedule(dynamic, 1) collapse(2)
+        for (int a = 0; a < ns; ++a)
+            for (int b = 0; b < ns; ++b)
+                for (int c = 0; c < ns; ++c)
+                    for (int d = 0; d < ns; ++d) {
+                        contract_tables(&bs, &q, a, b, c, d, nops, omegas, 0, NULL, NULL);
+                        const double *A = bs.xyz + 3 * bs.sh_atom[a], *Bc = bs.xyz + 3 * bs.sh_atom[b];
+                        const double *C = bs.xyz + 3 * bs.sh_atom[c], *D = bs.xyz + 3 * bs.sh_atom[d];
+                        double AB[3] = {A[0] - Bc[0], A[1] - Bc[1], A[2] - Bc[2]};
+                        double CD[3] = {C[0] - D[0], C[1] - D[1], C[2] - D[2]};
+                        int la = bs.sh_l[a], lb = bs.sh_l[b], lc = bs.sh_l[c], ld = bs.sh_l[d];
+                        for (int i = 0; i < ncart(la); ++i)
+                            for (int j = 0; j < ncart(lb); ++j)
+                                for (int k = 0; k < ncart(lc); ++k)
+                                    for (int l = 0; l < ncart(ld); ++l) {
+                                        int m = bs.bf_off[a] + i, n = bs.bf_off[b] + j;
+                                        int lam = bs.bf_off[c] + k, sig = bs.bf_off[d] + l;
+                                        int ta = tri_start[la] + i, tb = tri_start[lb] + j;
+                                        int tc = tri_start[lc] + k, td = tri_start[ld] + l;
+                                        double e0 = tab_int(&q, 0, 0, ta, tb, tc, td, AB, CD);
+                                        double e1 = nops > 1 ? tab_int(&q, 1, 0, ta, tb, tc, td, AB, CD) : 0.0;
+                                        for (int p = 0; p < npair; ++p) {
+                                            const double *Bp = Bm[p];
+                                            double clr = omega[p] > 0 ? cKlr[p] : 0.0;
+                                            Ft[(size_t)m * nbf + n] += cJ[p] * e0 * Bp[(size_t)lam * nbf + sig];
+#if OR_MUTATION == 15
+                                            Ft[(size_t)m * nbf + lam] += (cK[p] * e0 + clr * e1) * Bp[(size_t)sig * nbf + n];
+#else
+                                            Ft[(size_t)m * nbf + lam] += (cK[p] * e0 + clr * e1) * Bp[(size_t)n * nbf + sig];
+#endif
+                                        }
+                                    }
+                    }
+        ws_free(&q);
+    }
+    for (size_t k = 0; k < (size_t)nbf * nbf; ++k) {
+        double s = 0.0;
+        for (int t = 0; t < nth; ++t) s += acc[(size_t)t * nbf * nbf + k];
+        F[k] = s;
+    }
+    free(acc);
+    basis_free(&bs);
+    return 0;
+}

@@ -49,6 +49,16 @@ __host__ __device__ constexpr HermTriples make_herm_triples()
 }
 static __device__ const HermTriples kHermTriples = make_herm_triples();
 
+// v, negated when odd is 1 (a sign-bit flip on the integer pipe)
+__device__ __forceinline__ double flip_if(double v, int odd)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(odd & 1) << 63));
+}
+__device__ __forceinline__ float flip_if(float v, int odd)
+{
+    return __int_as_float(__float_as_int(v) ^ ((odd & 1) << 31));
+}
+
 __device__ __forceinline__ void herm_tuv(int h, int &t, int &u, int &v)
 {
     const unsigned w = kHermTriples.tuv[h];
@@ -124,7 +134,9 @@ struct WarpLayout {
     // m0, m1 (fp64: -2 rho, -2 rho th2; fp32: -1, -th2), zc2, s, then s^0 .. s^(L+2)
     static constexpr int SC_X = 0, SC_T = 3, SC_TH2 = 4, SC_PREF = 5, SC_MUL = 7, SC_ZC2 = 9, SC_S = 10,
                          SC_POW = 11;
-    static constexpr int NSC = SC_POW + L + 3;
+    // then, per operator, the base multipliers pref_op * mul_op^m for m <= L + 1
+    static constexpr int SC_PW = SC_POW + L + 3;
+    static constexpr int NSC = SC_PW + 2 * (L + 2);
     // ket primitive pairs whose 1-D tables and scalars are kept at a time
     static constexpr int QT_RAW = (int)((6144 / sizeof(F)) / (3 * EKN + NSC));
     static constexpr int QT = QT_RAW < 4 ? 4 : (QT_RAW > 32 ? 32 : QT_RAW);
@@ -306,6 +318,14 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                         sc_[Lay::SC_POW + k] = pw;
                         pw *= s;
                     }
+                    float b0 = pref, b1 = pref * sqrtf(th2);
+#pragma unroll
+                    for (int m = 0; m <= L + 1; ++m) {
+                        sc_[Lay::SC_PW + m] = b0;
+                        sc_[Lay::SC_PW + L + 2 + m] = b1;
+                        b0 = -b0;
+                        b1 *= -th2;
+                    }
                 } else {
                     const double p = pp.p[ip], q = pp.p[kp], pq = p + q, rho = p * q / pq;
                     const double X = pp.Px[ip] - pp.Px[kp], Y = pp.Py[ip] - pp.Py[kp], Z = pp.Pz[ip] - pp.Pz[kp];
@@ -324,6 +344,15 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                     sc_[Lay::SC_S] = 1.0;
 #pragma unroll
                     for (int k = 0; k <= L + 2; ++k) sc_[Lay::SC_POW + k] = 1.0;
+                    double b0 = pref, b1 = pref * sqrt(th2);
+                    const double m0 = -2.0 * rho, m1 = -2.0 * rho * th2;
+#pragma unroll
+                    for (int m = 0; m <= L + 1; ++m) {
+                        sc_[Lay::SC_PW + m] = b0;
+                        sc_[Lay::SC_PW + L + 2 + m] = b1;
+                        b0 *= m0;
+                        b1 *= m1;
+                    }
                 }
             }
             __syncwarp();
@@ -346,14 +375,7 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                         } else {
                             fm = boys_order_fp64(T, m, boys);
                         }
-                        // pref_op * mul_op^m
-                        F pw = sc_[Lay::SC_PREF + op], b = sc_[Lay::SC_MUL + op];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if ((m >> k) & 1) pw *= b;
-                            b *= b;
-                        }
-                        base[op * (L + 2) + m] = pw * fm;
+                        base[op * (L + 2) + m] = sc_[Lay::SC_PW + op * (L + 2) + m] * fm;
                     }
                 }
                 __syncwarp();
@@ -406,8 +428,9 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                     F e = F(0);
                     if (t <= cx + dx && u <= cy + dy && v <= cz + dz) {
                         e = Ek[(cx * KJ + dx) * KT + t] * Ek[EKN + (cy * KJ + dy) * KT + u] *
-                            Ek[2 * EKN + (cz * KJ + dz) * KT + v] * sc_[Lay::SC_POW + t + u + v];
-                        if ((t + u + v) & 1) e = -e;
+                            Ek[2 * EKN + (cz * KJ + dz) * KT + v];
+                        if constexpr (FP32) e *= sc_[Lay::SC_POW + t + u + v];
+                        e = flip_if(e, t + u + v);
                     }
                     E3k[it] = e;
                 }
@@ -479,7 +502,7 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                         F z = z0 + (nops == 2 ? z1 : F(0));
                         const int n2 = t2 + u2 + v2;
                         if constexpr (FP32) z *= sc_[Lay::SC_POW + n2];
-                        if (n2 & 1) z = -z;
+                        z = flip_if(z, n2);
                         const F ex = inx ? Ex[(cx * KJ + dx) * KT + t2] : F(0);
                         const F ey = iny ? Ey[(cy * KJ + dy) * KT + u2] : F(0);
                         const F ez = inz ? Ez[(cz * KJ + dz) * KT + v2] : F(0);

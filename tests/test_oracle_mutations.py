@@ -13,6 +13,7 @@ Pins used here (all independent of the oracle's own formulas):
   canonical   plain (all ordered quartets) = canonical (8 images/stabiliser)
   gamma       the paper's Gamma (eq. gamma) written as a 4-index tensor and
               contracted with the oracle's derivative integrals = the pair list
+  fock        the Fock-type build's trace against the canonical energy
   contraction a (pp|ps) quartet of 2-3-primitive shells of both operators
               against the quadrature of tests/test_oracle_contraction.py, with
               that file's own normalisation
@@ -45,6 +46,7 @@ MUTATIONS = {
     12: ("wrong sign in the upward Boys recursion (large T)", "boys"),
     13: ("coefficient of shell d taken at shell c's primitive index", "contraction"),
     14: ("first primitive's coefficient of shell b used for all its primitives", "contraction"),
+    15: ("Fock exchange block read with the density transposed", "fock"),
 }
 
 
@@ -197,7 +199,17 @@ def pin_contraction():
     return True
 
 
-PINS = {"gamma": pin_gamma, "contraction": pin_contraction, "boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
+def pin_fock():
+    s = synth.molecule(31, 1, 2)
+    n = s["pairs"][0][0].shape[0]
+    rng = np.random.default_rng(5)
+    A, B = rng.normal(size=(n, n)) / n, rng.normal(size=(n, n)) / n
+    F = oracle.fock2e(s, [(B, 0.4, 1.0, 0.6, 0.3)])
+    e = oracle.grad2e(s, pairs=[(A, B, 0.4, 1.0, 0.6, 0.3)], want_grad=False, want_energy=True)[1]
+    return abs(float(np.sum(A * F)) - e) <= 1e-12 * abs(e)
+
+
+PINS = {"gamma": pin_gamma, "contraction": pin_contraction, "fock": pin_fock, "boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
         "canonical": pin_canonical}
 
 
