@@ -199,6 +199,33 @@ int tg_grad2e(const tg_basis *b, int npair, const tg_pair *pairs, const tg_optio
 
 const char *tg_strerror(int status);
 
+/* ---- Fock-type build (Sec. II.B: the two-electron part of eq. G_2e, the
+ * Lagrangian's Fock-type matrices, and of eq. zfock, the Z-vector's; the XC
+ * kernel term of those equations is not part of it)
+ *
+ *   F[mu nu] = sum_p sum_{lam sig} B_p[lam sig] ( c_J (mu nu|lam sig)
+ *              + c_K (mu lam|nu sig) + c_K_lr (mu lam|nu sig)_omega )
+ *
+ * over npair (1..TG_MAX_PAIRS) density matrices B_p (nbf x nbf row-major,
+ * need not be symmetric; host pointers unless opt->device_ptrs).  Eq. G_2e
+ * is the pair (P~_delta^T; c_J = 2, c_K = -alpha, c_K_lr = -beta); eq. zfock
+ * is the two pairs (B^T; 4, -alpha, -beta) and (B; 0, -alpha, -beta).
+ * F: nbf*nbf doubles, overwritten.  Screening: a canonical shell quartet is
+ * skipped iff 8 * Q_ab Q_cd * M_q < screen_tol, with Q the Schwarz factors of
+ * tg_grad2e and M_q the largest over the blocks ab, cd, ac, ad, bc, bd (both
+ * orientations) of max(|S_J|, |B_K|, |B_lr|), S_J = sum_p c_J (B_p + B_p^T),
+ * B_K = sum_p c_K B_p, B_lr = sum_p c_K_lr B_p (omega > 0); screen_tol = 0
+ * keeps every quartet.  fp64 throughout (opt->precision must be TG_FP64);
+ * contributions are summed into F with fp64 atomics, so the last bits may
+ * change from run to run (opt->deterministic does not apply).  stats may be
+ * NULL (quartets, prim_quartets, class counts, timings as in tg_grad2e). */
+typedef struct {
+    const double *B;
+    double c_J, c_K, c_K_lr, omega;
+} tg_fpair;
+int tg_fock2e(const tg_basis *b, int npair, const tg_fpair *pairs, const tg_options *opt, double *F,
+              tg_stats *stats);
+
 /* ---- batched evaluation (many independent molecules, plan once, replay)
  * tg_batch_create plans every molecule (screening, class sort, routing as in
  * tg_grad2e) and captures one CUDA graph whose persistent class launches

@@ -34,7 +34,7 @@ TG_MAX_PAIRS = 8
 TG_SHARD_PAIR_KEY = 0
 TG_SHARD_TILES = 1
 
-EXPORTS = ("tg_options_default", "tg_abi_version", "tg_class_flops", "tg_tile_shard", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
+EXPORTS = ("tg_options_default", "tg_abi_version", "tg_class_flops", "tg_tile_shard", "tg_fock2e", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
            "tg_grad2e", "tg_strerror", "tg_tile_samples", "tg_router_nparam", "tg_router_create",
            "tg_router_destroy", "tg_router_get", "tg_router_set", "tg_router_train", "tg_router_loss_grad",
            "tg_router_predict", "tg_router_save", "tg_router_load", "tg_batch_create", "tg_batch_run",
@@ -45,6 +45,11 @@ NFEAT = 16
 class tg_pair(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("c_J", ctypes.c_double),
                 ("c_K", ctypes.c_double), ("c_K_lr", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class tg_fpair(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_void_p), ("c_J", ctypes.c_double), ("c_K", ctypes.c_double),
+                ("c_K_lr", ctypes.c_double), ("omega", ctypes.c_double)]
 
 
 class tg_options(ctypes.Structure):
@@ -262,6 +267,29 @@ class Basis:
             raise TGError(rc, "tg_tile_samples")
         return X[:n.value].copy(), y[:n.value].copy(), e[:n.value].copy()
 
+    def fock2e(self, pairs, screen_tol=0.0, timing=False, stream=None):
+        """Fock-type matrix (nbf x nbf) of host pairs [(B, c_J, c_K, c_K_lr, omega)]
+        (tg_fock2e) and the call's statistics."""
+        L = lib()
+        L.tg_fock2e.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tg_fpair), ctypes.POINTER(tg_options),
+                                ctypes.c_void_p, ctypes.POINTER(tg_stats)]
+        L.tg_fock2e.restype = ctypes.c_int
+        opt = tg_options_default()
+        opt.screen_tol = float(screen_tol)
+        opt.timing = 1 if timing else 0
+        if stream is not None:
+            opt.stream = ctypes.c_void_p(stream)
+        keep = [_c(b, np.float64) for (b, *_r) in pairs]
+        arr = (tg_fpair * len(pairs))(*[tg_fpair(k.ctypes.data, float(cj), float(ck), float(cl), float(om))
+                                        for k, (_b, cj, ck, cl, om) in zip(keep, pairs)])
+        n = keep[0].shape[0]
+        F = np.zeros((n, n))
+        st = tg_stats()
+        rc = L.tg_fock2e(self.h, len(pairs), arr, ctypes.byref(opt), ctypes.c_void_p(F.ctypes.data), ctypes.byref(st))
+        if rc != TG_OK:
+            raise TGError(rc, "tg_fock2e")
+        return F, st.as_dict()
+
     def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
                timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0, shard_mode=0):
         """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
@@ -306,6 +334,14 @@ class Basis:
         if rc != TG_OK:
             raise TGError(rc, "tg_grad2e")
         return g, st.as_dict()
+
+
+def zfock_pairs(B, alpha, beta, omega):
+    """The Z-vector's Fock-type matrix of eq. zfock (Sec. II.B, without the XC
+    kernel term) as tg_fock2e pairs: sum_{lam sig} B[sig lam] [4 (mu nu|lam sig)
+    - alpha ((mu lam|sig nu) + (mu sig|lam nu)) - beta (same)_lr] is the pair
+    (B^T; 4, -alpha, -beta) plus (B; 0, -alpha, -beta)."""
+    return [(np.ascontiguousarray(np.asarray(B).T), 4.0, -alpha, -beta, omega), (B, 0.0, -alpha, -beta, omega)]
 
 
 def tda_pairs(P, P_delta, R, alpha, beta, omega):

@@ -85,6 +85,7 @@ struct tg_basis {
     double *d_bp = nullptr;        // primitive-pair bounds b_kl (larger shell index first)
     DevArena ws1, ws2;
     DevArena ws3, ws4;  // device tile planner: per-class tile maxima and rows; tile lists
+    DevArena ws5;       // Fock build: densities, combined matrices, F
     float *d_router = nullptr;  // router parameters, mean and std on the device
     int nsm = 0;
 };
@@ -126,6 +127,7 @@ void free_basis(tg_basis *b)
     b->ws2.release();
     b->ws3.release();
     b->ws4.release();
+    b->ws5.release();
 }
 
 int basis_setup(tg_basis *b, const double *xyz, const double *exps, const double *coefs)
@@ -350,6 +352,7 @@ struct Plan {
     std::vector<HostTile> tiles;
     int qc_P[NQC], qc_Q[NQC];
     unsigned class_mask = 0;
+    bool fock = false;  // Fock build: linear bounds, Q only
     int launches = 0;
     int G = 1;
     PairSet set(int c) const
@@ -402,7 +405,7 @@ int check_pairs(int npair, const tg_pair *pairs, const tg_options &opt, double &
 
 // Densities, block factors, screened pairs, primitive pairs, unrouted tiles.
 int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &opt, cudaStream_t st, Plan &pl,
-              bool host_tiles = true)
+              bool host_tiles = true, bool fock = false)
 {
     double omega;
     int use_lr;
@@ -474,14 +477,17 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
 
     // ---- pair screening and class sort (Sec. II.C: presort by K and the Schwarz bound)
     pl.tau = opt.screen_tol;
-    pl.scale = 8.0 * npair;
+    // gradient: 8 npair max(Q' Q, Q Q') M^2; Fock build: 8 Q Q M (see tdgrad.h)
+    pl.fock = fock;
+    pl.scale = fock ? 8.0 : 8.0 * npair;
     const double tau = pl.tau, scale = pl.scale;
     for (int x = 0; x < ns; ++x)
         for (int y = 0; y <= x; ++y) {
             const long long k = pkey(x, y);
             const double q = b->Q[(size_t)k], qd = b->Qd[(size_t)k];
             if (tau > 0.0) {
-                const double bnd = scale * std::max(qd * b->Qmax, q * b->Qdmax) * Mmax * Mmax;
+                const double bnd = fock ? scale * q * b->Qmax * Mmax
+                                        : scale * std::max(qd * b->Qmax, q * b->Qdmax) * Mmax * Mmax;
                 if (bnd < tau) continue;
             }
             int sa = x, sb = y;
@@ -496,8 +502,11 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
             pl.cls[pair_class(b->sh_l[sa], b->sh_l[sb])].push_back(hp);
         }
     // surviving primitive pairs per kept shell pair (primitive screen, see tdgrad.h)
+    // (the kernels test scale * b_kl * qq * m^2 < eps_p; the Fock build's linear
+    // bound scale * b_kl * Qmax * Mmax takes m = sqrt(Mmax))
     const double eps_p = tau > 0.0 ? 1e-6 * tau : 0.0;
-    const double qq = std::max(b->Qmax, b->Qdmax);
+    const double qq = fock ? b->Qmax : std::max(b->Qmax, b->Qdmax);
+    const double Mp = fock ? std::sqrt(Mmax) : Mmax;
     long long nk_all = 0, npp_max = 0;
     for (int c = 0; c < NPC; ++c) {
         nk_all += (long long)pl.cls[c].size();
@@ -545,7 +554,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
             TG_CUDA(cudaMemcpyAsync(pl.d_key, u_key.data(), sizeof(int) * nk_all, cudaMemcpyHostToDevice, st));
             k_prim_count<<<(unsigned)((nk_all + 127) / 128), 128, 0, st>>>((int)nk_all, pl.d_sa, pl.d_sb, pl.d_key,
                                                                            b->d_sh_nprim, b->d_bpoff, b->d_bp, scale,
-                                                                           qq, Mmax, eps_p, d_cnt);
+                                                                           qq, Mp, eps_p, d_cnt);
             ++pl.launches;
             TG_CUDA(cudaGetLastError());
             std::vector<int> cnt((size_t)nk_all);
@@ -651,7 +660,7 @@ int make_plan(tg_basis *b, int npair, const tg_pair *pairs, const tg_options &op
         TG_CUDA(cudaMemcpyAsync(pl.d_Qd, h_Qd.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
         k_prim_pairs<<<(unsigned)((nk + 127) / 128), 128, 0, st>>>(
             (int)nk, pl.d_sa, pl.d_sb, pl.d_poff, pl.d_key, b->d_xyz, b->d_sh_atom, b->d_sh_nprim, b->d_sh_poff,
-            b->d_exps, b->d_cn, b->d_bpoff, b->d_bp, scale, qq, Mmax, eps_p, pp_p, pp_x, pp_y, pp_z, pp_K, pp_za, fp_p,
+            b->d_exps, b->d_cn, b->d_bpoff, b->d_bp, scale, qq, Mp, eps_p, pp_p, pp_x, pp_y, pp_z, pp_K, pp_za, fp_p,
             fp_x, fp_y, fp_z, fp_K, fp_za, fp_PA, fp_PB, (long long)npp);
         ++pl.launches;
         TG_CUDA(cudaGetLastError());
@@ -860,6 +869,7 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
     ra.nrows = nrows;
     ra.tau = pl.tau;
     ra.scale = pl.scale;
+    ra.fock = pl.fock ? 1 : 0;
     for (int qc = 0; qc < NQC; ++qc) {
         ra.qcP[qc] = pl.qc_P[qc];
         ra.qcQ[qc] = pl.qc_Q[qc];
@@ -1267,6 +1277,141 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
     TG_CUDA(cudaStreamSynchronize(st));
     if (stats) {
         fill_stats(stats, hc, pl.npairs_kept, (long long)ntl, launches, pl.G, pl.den.use_lr ? 2 : 1);
+        stats->plan_ms = plan_ms;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return TG_OK;
+}
+
+int tg_fock2e(const tg_basis *cb, int npair, const tg_fpair *fpairs, const tg_options *opt_in, double *F,
+              tg_stats *stats)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    tg_basis *b = const_cast<tg_basis *>(cb);
+    if (!b || !fpairs || !F) return TG_EINVAL;
+    tg_options opt;
+    if (opt_in) opt = *opt_in;
+    else tg_options_default(&opt);
+    if (npair < 1) return TG_EINVAL;
+    if (npair > TG_MAX_PAIRS) return TG_EUNSUPPORTED;
+    if (!(opt.screen_tol >= 0.0) || !std::isfinite(opt.screen_tol)) return TG_EINVAL;
+    if (opt.precision != TG_FP64 || opt.nranks != 1 || opt.rank != 0) return TG_EUNSUPPORTED;
+    if (opt.class_mask >> NQC) return TG_EINVAL;
+    for (int r : opt.reserved)
+        if (r != 0) return TG_EINVAL;
+    double omega = 0.0;
+    int use_lr = 0;
+    for (int p = 0; p < npair; ++p) {
+        const tg_fpair &q = fpairs[p];
+        if (!q.B) return TG_EINVAL;
+        if (!std::isfinite(q.c_J) || !std::isfinite(q.c_K) || !std::isfinite(q.c_K_lr) || std::isnan(q.omega))
+            return TG_EINVAL;
+        if (q.c_K_lr != 0.0 && q.omega > 0.0) {
+            if (use_lr && q.omega != omega) return TG_EUNSUPPORTED;
+            use_lr = 1;
+            omega = q.omega;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)opt.stream;
+    TG_CUDA(cudaSetDevice(b->device));
+    const int nbf = b->nbf, natom = b->natom;
+    const size_t nbf2 = (size_t)nbf * nbf;
+    // densities (device copies of host matrices), the combined matrices and F
+    DevArena &Z = b->ws5;
+    const int nup = opt.device_ptrs ? 0 : npair;
+    TG_CUDA(Z.reserve(al(sizeof(double) * nbf2) * (nup + 4) + 4096));
+    Z.used = 0;
+    DensArgs dn;
+    std::memset(&dn, 0, sizeof(dn));
+    dn.npair = npair;
+    dn.nbf = nbf;
+    for (int p = 0; p < npair; ++p) {
+        if (opt.device_ptrs) {
+            dn.A[p] = fpairs[p].B;
+        } else {
+            double *d = Z.take<double>(nbf2);
+            TG_CUDA(cudaMemcpyAsync(d, fpairs[p].B, sizeof(double) * nbf2, cudaMemcpyHostToDevice, st));
+            dn.A[p] = d;
+        }
+        dn.cJ[p] = fpairs[p].c_J;
+        dn.cK[p] = fpairs[p].c_K;
+        dn.cKlr[p] = fpairs[p].omega > 0.0 ? fpairs[p].c_K_lr : 0.0;
+    }
+    double *SJ = Z.take<double>(nbf2), *BK = Z.take<double>(nbf2), *BL = Z.take<double>(nbf2);
+    double *dF = Z.take<double>(nbf2);
+    const unsigned gs = (unsigned)((nbf2 + 255) / 256);
+    k_fock_combine<<<gs, 256, 0, st>>>(nbf, dn, SJ, BK, BL);
+    TG_CUDA(cudaMemsetAsync(dF, 0, sizeof(double) * nbf2, st));
+    TG_CUDA(cudaGetLastError());
+    // plan over the combined matrices: M = max(|S_J|, |B_K|, |B_lr|) per shell block
+    tg_pair pseudo[2];
+    pseudo[0] = {SJ, BK, 1.0, 0.0, 0.0, 0.0};
+    pseudo[1] = {BL, BL, 1.0, 0.0, 0.0, 0.0};
+    tg_options po = opt;
+    po.device_ptrs = 1;
+    po.precision = TG_FP64;
+    po.nranks = 1;
+    po.rank = 0;
+    Plan pl;
+    int rc = make_plan(b, 2, pseudo, po, st, pl, false, true);
+    if (rc != TG_OK) return rc;
+    pl.den.use_lr = use_lr;
+    pl.den.omega = omega;
+    pl.scr.scale = pl.scale;
+    int launches = pl.launches + 1;
+    DevArena &V = b->ws2;
+    MolDesc *d_mol = V.take<MolDesc>(1);
+    DevTiles dt;
+    rc = device_tiles(b, pl, po, st, dt, launches);
+    if (rc != TG_OK) return rc;
+    const MolDesc md = make_desc(pl, 0);
+    TG_CUDA(cudaMemcpyAsync(d_mol, &md, sizeof(MolDesc), cudaMemcpyHostToDevice, st));
+    TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * NCNT * NQC, st));
+    if (stats)
+        for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
+    const double plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    EventPair ev;
+    if (opt.timing) TG_CUDA(ev.create());
+    for (int qc = 0; qc < NQC; ++qc) {
+        const long long nt = dt.off[2 * qc + 1] - dt.off[2 * qc];
+        if (nt <= 0) continue;
+        ClassLaunch cl;
+        std::memset(&cl, 0, sizeof(cl));
+        cl.P = pl.qc_P[qc];
+        cl.Q = pl.qc_Q[qc];
+        cl.ntiles = nt;
+        cl.tiles = dt.tiles + dt.off[2 * qc];
+        cl.stride = 1;
+        cl.nsplit = cl.nchunk = 1;
+        OutArgs o;
+        std::memset(&o, 0, sizeof(o));
+        o.counters = pl.dcnt + NCNT * qc;
+        o.natom_total = o.natom_max = natom;
+        o.fock = dF;
+        if (opt.timing) cudaEventRecord(ev.a, st);
+        cudaError_t e = kFockLaunchers[qc](pl.G, st, d_mol, cl, o, b->d_boys);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return TG_ECUDA;
+        }
+        ++launches;
+        if (opt.timing) {
+            cudaEventRecord(ev.b, st);
+            cudaEventSynchronize(ev.b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev.a, ev.b);
+            if (stats) stats->class_ms[qc] += ms;
+        }
+    }
+    unsigned long long hc[NCNT * NQC];
+    TG_CUDA(cudaMemcpyAsync(hc, pl.dcnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaMemcpyAsync(F, dF, sizeof(double) * nbf2,
+                            opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        fill_stats(stats, hc, pl.npairs_kept, dt.ntiles, launches, pl.G, use_lr ? 2 : 1);
+        stats->fp64_flop = 0.0;  // the gradient's FLOP count does not apply
+        stats->fp64_frac_peak = 0.0;
         stats->plan_ms = plan_ms;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }

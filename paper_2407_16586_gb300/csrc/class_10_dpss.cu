@@ -1,5 +1,5 @@
 // (dp|ss) derivative-ERI class kernel instance.
-#include "eri_warp.cuh"
+#include "eri_fock.cuh"
 
 namespace tg {
 
@@ -7,6 +7,12 @@ cudaError_t launch_qc10(int fp32, int grid, size_t smem, cudaStream_t st, const 
                          const ClassLaunch &cl, const OutArgs &out, const double *boys)
 {
     return launch_class_kernel<2, 1, 0, 0>(fp32, grid, smem, st, mols, cl, out, boys);
+}
+
+cudaError_t launch_fock_qc10(int grid, cudaStream_t st, const MolDesc *mols, const ClassLaunch &cl,
+                             const OutArgs &out, const double *boys)
+{
+    return launch_fock_class<2, 1, 0, 0>(grid, st, mols, cl, out, boys);
 }
 
 }  // namespace tg

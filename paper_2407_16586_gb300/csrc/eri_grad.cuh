@@ -887,14 +887,14 @@ __global__ void __launch_bounds__(TILE) k_grad(const MolDesc *__restrict__ mols,
 // GPU.  Dump mode keeps one unit per tile.
 template <typename K>
 cudaError_t launch_units(K kern, int ngroups, int gcap, size_t sm, cudaStream_t st, const MolDesc *mols,
-                         ClassLaunch cl, const OutArgs &out, const double *boys)
+                         ClassLaunch cl, const OutArgs &out, const double *boys, int block = TILE)
 {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 1, per = 1;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TILE, sm)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, sm)) != cudaSuccess) return e;
     long long gmax = (long long)(per > 0 ? per : 1) * nsm;
     if (gmax > gcap) gmax = gcap;
     cl.nchunk = 1;
@@ -907,7 +907,7 @@ cudaError_t launch_units(K kern, int ngroups, int gcap, size_t sm, cudaStream_t 
     }
     const long long units = cl.ntiles * cl.nchunk * cl.nsplit;
     const int grid = (int)(units < gmax ? units : gmax);
-    kern<<<grid, TILE, sm, st>>>(mols, cl, out, boys);
+    kern<<<grid, block, sm, st>>>(mols, cl, out, boys);
     return cudaGetLastError();
 }
 

@@ -72,13 +72,13 @@ __global__ void k_tile_rows(RowArgs a, int mode, int *count, const long long *of
     for (int g = k0 / GROUP; g * GROUP < nkt; ++g) {
         if (a.tau > 0.0) {
             const double Mt = fmax(m, K.gm[g]);
-            const double b = a.scale * fmax(qd * K.gq[g], q * K.gqd[g]) * Mt * Mt;
+            const double b = a.fock ? a.scale * q * K.gq[g] * Mt : a.scale * fmax(qd * K.gq[g], q * K.gqd[g]) * Mt * Mt;
             if (b < a.tau) continue;
         }
         const int hi = min(nkt, (g + 1) * GROUP);
         for (int kt = max(k0, g * GROUP); kt < hi; ++kt) {
             const double Mt = fmax(m, K.km[kt]);
-            const double b = a.scale * fmax(qd * K.kq[kt], q * K.kqd[kt]) * Mt * Mt;
+            const double b = a.fock ? a.scale * q * K.kq[kt] * Mt : a.scale * fmax(qd * K.kq[kt], q * K.kqd[kt]) * Mt * Mt;
             if (a.tau > 0.0 && b < a.tau) continue;
             if (mode) {
                 tiles[o + c] = make_uint4(0u, (unsigned)bt, (unsigned)kt, (unsigned)qc);

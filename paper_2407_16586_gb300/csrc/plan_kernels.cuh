@@ -24,6 +24,7 @@ struct RowArgs {
     TileMaxima t[NPC];
     int qcP[NQC], qcQ[NQC];
     double tau, scale;
+    int fock;  // 1: Fock-build bound scale * Q_bt Q_kt * max(M_bt, M_kt)
 };
 
 // Routing bins: 8 per octave of the fp32 error estimate e; bin 0 holds e <= 2^-1000.

@@ -331,6 +331,25 @@ __global__ void k_symm(int nbf, const double *A, double *S)
     S[id] = A[id] + A[(size_t)c * nbf + r];
 }
 
+// Combined density matrices of the Fock build: S_J = sum_p c_J (B_p + B_p^T),
+// B_K = sum_p c_K B_p, B_lr = sum_p c_K_lr B_p (pairs in order).
+__global__ void k_fock_combine(int nbf, DensArgs den, double *SJ, double *BK, double *BL)
+{
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)nbf * nbf) return;
+    const int r = (int)(id / nbf), c = (int)(id % nbf);
+    double sj = 0.0, bk = 0.0, bl = 0.0;
+    for (int p = 0; p < den.npair; ++p) {
+        const double v = den.A[p][id], vt = den.A[p][(size_t)c * nbf + r];
+        sj += den.cJ[p] * (v + vt);
+        bk += den.cK[p] * v;
+        bl += den.cKlr[p] * v;
+    }
+    SJ[id] = sj;
+    BK[id] = bk;
+    BL[id] = bl;
+}
+
 // grad[k] = sum_c partials[c][k] in the fixed order c = 0..nslab-1
 __global__ void k_reduce(int n, int nslab, const double *partials, double *grad)
 {

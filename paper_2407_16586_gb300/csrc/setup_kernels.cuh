@@ -22,6 +22,7 @@ __global__ void k_prim_pairs(int npairs, const int *psa, const int *psb, const i
                              double *Pz, double *K, double *za_, float *fp, float *fPx, float *fPy, float *fPz,
                              float *fK, float *fza, float *fPA, float *fPB, long long nrec);
 __global__ void k_symm(int nbf, const double *A, double *S);
+__global__ void k_fock_combine(int nbf, DensArgs den, double *SJ, double *BK, double *BL);
 __global__ void k_reduce(int n, int nslab, const double *partials, double *grad);
 
 }  // namespace tg

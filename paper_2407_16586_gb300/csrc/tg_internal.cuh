@@ -111,6 +111,7 @@ struct OutArgs {
     unsigned long long *counters;     // NCNT per class (see NCNT)
     int use_smem;                     // per-molecule partial gradient kept in shared memory
     double *dump;                     // nullable: per-quartet gradients [tile][TILE][12] instead of reducing
+    double *fock;                     // Fock build: the nbf x nbf output (atomic adds)
 };
 
 // Deterministic reduction of one staged tile into the per-molecule partial

@@ -78,3 +78,20 @@ def test_omega_infinity_and_symmetry(small):
     Fj = oracle.fock2e(small, [(B, 1.0, 0.0, 0.0, 0.0)])
     assert np.abs(Fj - Fj.T).max() <= 1e-12 * np.abs(Fj).max()
     assert np.abs(Fk - Fk.T).max() <= 1e-12 * np.abs(Fk).max()
+
+
+def test_zfock_pair_mapping():
+    """The binding's zfock_pairs against eq. zfock written out with the
+    4-index integral tensor: sum_{lam sig} B[sig lam] (4 (mu nu|lam sig)
+    - alpha ((mu lam|sig nu) + (mu sig|lam nu)) - beta (...)_lr)."""
+    import paper_2407_16586_gb300 as tg
+    s = synth.molecule(33, 1, 1)
+    nbf = s["pairs"][0][0].shape[0]
+    eri, erl = _full_eri(s), _full_eri(s, 0.3)
+    B = _rand(nbf, 7)
+    a, b = 0.157706, 0.842294
+    ref = (4 * np.einsum("mnls,sl->mn", eri, B)
+           - a * (np.einsum("mlsn,sl->mn", eri, B) + np.einsum("msln,sl->mn", eri, B))
+           - b * (np.einsum("mlsn,sl->mn", erl, B) + np.einsum("msln,sl->mn", erl, B)))
+    F = oracle.fock2e(s, tg.zfock_pairs(B, a, b, 0.3))
+    assert np.abs(F - ref).max() <= 1e-12 * np.abs(ref).max()
