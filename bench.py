@@ -322,11 +322,14 @@ def run_c3(args, prec, router, torch):
 
 
 def run_large(args, prec, router, torch):
-    """The 300-atom c4 cluster: one step takes minutes, so the kernels are
+    """The 300-atom c4 cluster: one step takes many minutes, so the kernels are
     warmed on c1, then ONE mixed step and ONE fp64 step are timed (CUDA events
     on the launching stream, per-class events on), and the fp64 gradient is
-    the reference of the mixed one.  No end-to-end repeat (the host copies
-    are 0.2 GB against minutes of kernels)."""
+    the reference of the mixed one.  With --shard N both steps evaluate the
+    tile-cyclic shard 0 of N (every class list dealt round-robin, so the shard
+    holds 1/N of every class's cost-ordered tiles) and the full-gradient time
+    is reported as N times the shard's; the router spends the whole mixed_tol
+    budget on the shard's tiles.  No end-to-end repeat."""
     import numpy as np
     import paper_2407_16586_gb300 as tg
     from paper_2407_16586_gb300 import synth
@@ -342,13 +345,16 @@ def run_large(args, prec, router, torch):
               for (a, b, cj, ck, cl, om) in s["pairs"]]
     gout = torch.empty((s["natom"], 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    nsh = max(1, args.shard)
+    shard = dict(rank=0, nranks=nsh, shard_mode=tg.TG_SHARD_TILES) if nsh > 1 else {}
 
     def one(precision):
         flush.zero_()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=True)
+        _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=True,
+                             **shard)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1), st, gout.cpu().numpy().copy()
@@ -368,12 +374,52 @@ def run_large(args, prec, router, torch):
                        "quartets_per_step": st["quartets"], "fp32_quartets_per_step": st["fp32_quartets"],
                        "prim_quartets_per_step": st["prim_quartets"], "pairs": st["pairs"], "tiles": st["tiles"],
                        "warm-up": "two c1 calls (kernels and context loaded); one timed step per precision",
+                       "shard": ("tile-cyclic shard 0 of %d" % nsh) if nsh > 1 else "whole gradient",
+                       "full_gradient_s_estimate": {"mixed": nsh * ms / 1e3, "fp64": nsh * ms64 / 1e3},
                        "l2": "flushed (512 MB write) before each timed step"},
             "e2e": None, "gpu_launches": st["launches"], "plan_ms": st["plan_ms"],
             "roofline": roofline_entry(st), "clocks": _clocks_summary(rows, 0),
             "fp64": {"ms_per_step": ms64, "value": st64["quartets"] / (ms64 / 1e3),
                      "max_abs_dg_vs_fp64": float(np.abs(g - g64).max()), "speedup_vs_fp64": ms64 / ms,
                      "roofline": roofline_entry(st64), "plan_ms": st64["plan_ms"]}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_fock(args, torch):
+    """The Fock-type build on the same workload (Sec. II.B, eq. G_2e: the
+    relaxed difference density with c_J = 2, c_K = -alpha, c_K_lr = -beta;
+    eq. zfock: a transition-like density through its two pairs), timed like
+    the gradient step; metric: canonical quartets of the build per second."""
+    import numpy as np
+    import paper_2407_16586_gb300 as tg
+    s, wname = workload(args.workload)
+    dev = torch.device("cuda", 0)
+    basis = tg.Basis(s)
+    a, b = 0.157706, 0.842294
+    P, Pd, X = s["pairs"][0][0], s["pairs"][1][0], s["pairs"][2][0]
+    pairs = [(Pd.T.copy(), 2.0, -a, -b, 0.3)] + tg.zfock_pairs(X, a, b, 0.3)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        F, st0 = basis.fock2e(pairs, screen_tol=TAU)
+    _, st_t = basis.fock2e(pairs, screen_tol=TAU, timing=True)
+    ms, q = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        F, st = basis.fock2e(pairs, screen_tol=TAU)
+        ms.append(1e3 * (time.perf_counter() - t))
+        q += st["quartets"]
+    line = {"metric": "Fock-type build quartets/s (canonical shell quartets after screening)",
+            "value": q / (sum(ms) / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sum(ms) / len(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname + "; Fock build of eq. G_2e (P_delta^T) + eq. zfock (X)",
+                       "screen_tol": TAU, "quartets_per_step": st0["quartets"],
+                       "prim_quartets_per_step": st0["prim_quartets"],
+                       "timing": "host clock around tg_fock2e with host densities in and F out (end to end)"},
+            "class_ms": st_t["class_ms"], "plan_ms": st_t["plan_ms"], "gpu_launches": st0["launches"]}
     print(json.dumps(line))
     return 0
 
@@ -392,12 +438,14 @@ def main():
     ap.add_argument("--workload", default="c2", help='c2 (default), c1, c3, c3:N, c4, or chain:SEED:NHEAVY:NH')
     ap.add_argument("--bound-steps", type=int, default=1, help="timed mixed-bound steps for the comparison (0: skip)")
     ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
+    ap.add_argument("--fock", action="store_true", help="time the Fock-type build (tg_fock2e) instead")
+    ap.add_argument("--shard", type=int, default=1, help="c4: time tile-cyclic shard 0 of this many")
     args = ap.parse_args()
     if args.opcount:
         print_opcount()
         return 0
     # c4 steps take minutes each: one warm-up step (the default c2 line keeps >= 3)
-    args.warmup = max(args.warmup, 1 if args.workload == "c4" else 3)
+    args.warmup = max(args.warmup, 1 if args.workload == "c4" or args.workload.startswith("c3") else 3)
     if args.ref_shards is None:
         args.ref_shards = 50000 if args.workload == "c4" else 600
     if args.impl == "reference":
@@ -425,6 +473,8 @@ def main():
             "fp32": tg.TG_FP32}[args.precision]
     router = tg.Router(path=args.router) if prec == tg.TG_MIXED_LEARNED else None
 
+    if args.fock:
+        return run_fock(args, torch)
     if args.workload.startswith("c3"):
         return run_c3(args, prec, router, torch)
     if args.workload == "c4":
@@ -541,6 +591,8 @@ def main():
             "gpu_launches": launches,
             "roofline": roofline_entry(st_t),
             "plan_ms": st_t["plan_ms"],
+            "class_ms": {"fp64": [round(x, 2) for x in st_t["class_ms"]],
+                         "fp32": [round(x, 2) for x in st_t["class_ms_fp32"]]},
             "clocks": _clocks_summary(rows, local),
         }
         if fp64 is not None:

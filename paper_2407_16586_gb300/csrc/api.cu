@@ -1084,7 +1084,7 @@ void build_exec(const std::vector<const Plan *> &plans, const std::vector<std::v
 int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, double *d_part,
                 unsigned long long *dcnt, double *dump, const double *boys, int G, const int *grids, bool timing,
                 cudaStream_t st, tg_stats *stats, int &launches, const int *kinds = nullptr, int kind_all = 0,
-                int tile_rank = 0, int tile_nranks = 1)
+                int tile_rank = 0, int tile_nranks = 1, const int *splits = nullptr)
 {
     OutArgs out;
     out.partials = d_part;
@@ -1122,6 +1122,7 @@ int launch_exec(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, dou
             cl.stride = stride;
             cl.nsplit = cl.nchunk = 1;
             cl.kind = kinds ? kinds[k] : kind_all;
+            cl.split_req = splits ? splits[k] : 0;
             OutArgs o = out;
             o.counters = dcnt + NCNT * qc;
             if (dump) o.dump = dump + (size_t)ex.off[k] * TILE * 12;
@@ -1215,7 +1216,7 @@ struct tg_batch {
     uint4 *d_tiles = nullptr;
     double *d_part = nullptr, *d_grad = nullptr;
     unsigned long long *d_cnt = nullptr;
-    std::vector<int> grids, kinds;
+    std::vector<int> grids, kinds, splits;
     int G = 1;
     int device_ptrs = 0;
     cudaStream_t cap = nullptr;
@@ -1594,10 +1595,12 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
     const double *boys = bt->bases[0]->d_boys;
 
     // ---- autotune every (class, precision) list on a sample of its tiles:
-    // thread or cooperative kernel, grid capped at 1, 2, 3 or 4 CTAs per SM;
-    // the fastest pair is kept
+    // kernel form (thread, group, warp), grid capped at 1, 2 or 4 CTAs per SM,
+    // and unit shape (bra-primitive splits per tile: automatic, 1 or 4); the
+    // fastest combination is kept
     bt->grids.assign(2 * NQC, G);
     bt->kinds.assign(2 * NQC, opt.kernel_kind);
+    bt->splits.assign(2 * NQC, 0);
     const int nsm = std::max(1, bt->bases[0]->nsm);
     if (opt.autotune == 1) {
         EventPair ev;
@@ -1612,13 +1615,15 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
             const long long ns = std::min<long long>(nt, 8LL * nsm);
             for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : ns;
             float best = -1.f;
-            for (int kind = 1; kind <= 2; ++kind)
-                for (int mult = 1; mult <= 4; ++mult) {
-                    std::vector<int> gr(2 * NQC, mult * nsm), kd(2 * NQC, kind);
+            for (int kind = 1; kind <= 3; ++kind)
+                for (int mult : {1, 2, 4})
+                    for (int split : {0, 1, 4}) {
+                    std::vector<int> gr(2 * NQC, mult * nsm), kd(2 * NQC, kind), sp(2 * NQC, split);
                     int dummy = 0;
                     cudaEventRecord(e0, st);
                     int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt,
-                                         nullptr, boys, G, gr.data(), false, st, nullptr, dummy, kd.data());
+                                         nullptr, boys, G, gr.data(), false, st, nullptr, dummy, kd.data(), 0, 0, 1,
+                                         sp.data());
                     cudaEventRecord(e1, st);
                     if (rc != TG_OK) return rc;
                     TG_CUDA(cudaEventSynchronize(e1));
@@ -1628,8 +1633,9 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
                         best = ms;
                         bt->grids[k] = mult * nsm;
                         bt->kinds[k] = kind;
+                        bt->splits[k] = split;
                     }
-                }
+                    }
         }
         bt->G = G = std::max(G, *std::max_element(bt->grids.begin(), bt->grids.end()));
     }
@@ -1661,7 +1667,8 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
         cudaMemsetAsync(bt->d_part, 0, sizeof(double) * (size_t)G * 3 * natom_total, bt->cap);
         cudaMemsetAsync(bt->d_cnt, 0, sizeof(unsigned long long) * NCNT * NQC, bt->cap);
         int rc = launch_exec(bt->ex, bt->d_mols, bt->d_tiles, bt->d_part, bt->d_cnt, nullptr, boys, G,
-                             bt->grids.data(), false, bt->cap, nullptr, n, bt->kinds.data());
+                             bt->grids.data(), false, bt->cap, nullptr, n, bt->kinds.data(), 0, 0, 1,
+                             bt->splits.data());
         k_reduce<<<(3 * natom_total + 127) / 128, 128, 0, bt->cap>>>(3 * natom_total, G, bt->d_part, bt->d_grad);
         ++n;
         if (pass == 1) {

@@ -904,6 +904,7 @@ cudaError_t launch_units(K kern, int ngroups, int gcap, size_t sm, cudaStream_t 
         if (ngroups > 0)
             while (cl.ntiles * cl.nchunk < want && cl.nchunk * ngroups < TILE) cl.nchunk *= 2;
         while (cl.ntiles * cl.nchunk * cl.nsplit < want && cl.nsplit < 4) ++cl.nsplit;
+        if (cl.split_req > 0) cl.nsplit = cl.split_req;
     }
     const long long units = cl.ntiles * cl.nchunk * cl.nsplit;
     const int grid = (int)(units < gmax ? units : gmax);

@@ -101,7 +101,8 @@ struct ClassLaunch {
     long long stride;          // 1, or nranks for tile-cyclic shards
     int nsplit;                // units per tile along the bra primitive pairs (>= 1)
     int nchunk;                // cooperative kernel: quartet chunks per tile (divides TILE / groups)
-    int kind;                  // 0: default kernel of the class, 1: thread kernel, 2: cooperative kernel
+    int kind;                  // 0: default form of the class, 1: thread, 2: group, 3: warp
+    int split_req;             // bra-primitive splits per tile requested by the autotuner (0: automatic)
 };
 
 struct OutArgs {
