@@ -327,9 +327,12 @@ def run_large(args, prec, router, torch):
     on the launching stream, per-class events on), and the fp64 gradient is
     the reference of the mixed one.  With --shard N both steps evaluate the
     tile-cyclic shard 0 of N (every class list dealt round-robin, so the shard
-    holds 1/N of every class's cost-ordered tiles) and the full-gradient time
-    is reported as N times the shard's; the router spends the whole mixed_tol
-    budget on the shard's tiles.  No end-to-end repeat."""
+    holds 1/N of every class's cost-ordered tiles, dealt before the fp32 /
+    fp64 split, so both steps evaluate the same tiles) and the full-gradient
+    time is reported as N times the shard's.  The route is the whole
+    gradient's (the mixed_tol budget covers all N shards), so the shard's
+    max|dg| against fp64 is the error of 1/N of the tiles.  No end-to-end
+    repeat."""
     import numpy as np
     import paper_2407_16586_gb300 as tg
     from paper_2407_16586_gb300 import synth

@@ -125,14 +125,17 @@ typedef struct {
 
 /* tg_options.shard_mode with nranks > 1:
  * TG_SHARD_PAIR_KEY: the quartet shards of the top of this file (pair keys mod nranks).
- * TG_SHARD_TILES: every (class, precision) launch list, ordered by decreasing cost, is
- *   dealt cyclically: its tile i belongs to rank i mod nranks.  Each rank then runs 1/nranks
- *   of every class's tiles (balanced cost, no quartet filter inside the kernels); the
- *   partial gradients of all ranks sum to the full one.  tg_grad2e only. */
+ * TG_SHARD_TILES: the screened tile list of every angular class, in the planner's order
+ *   (decreasing cost), is dealt cyclically BEFORE the fp32 / fp64 split: its tile i
+ *   belongs to rank i mod nranks.  The route is the one of the whole call (the mixed_tol
+ *   budget covers all ranks' tiles together), and a rank holds the same tiles at every
+ *   precision, so its fp32 / mixed partial can be checked against its fp64 partial.  Each
+ *   rank runs 1/nranks of every class's tiles (balanced cost, no quartet filter inside the
+ *   kernels); the partial gradients of all ranks sum to the full one.  tg_grad2e only. */
 #define TG_SHARD_PAIR_KEY 0
 #define TG_SHARD_TILES 1
 
-/* The tiles of one launch list of ntiles tiles that rank evaluates under
+/* The tiles of one class list of ntiles screened tiles that rank evaluates under
  * TG_SHARD_TILES: *count tiles, first, first + stride, ...  Host only. */
 int tg_tile_shard(long long ntiles, int rank, int nranks, long long *first, long long *count, long long *stride);
 

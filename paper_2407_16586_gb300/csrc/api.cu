@@ -875,7 +875,7 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
         ra.qcQ[qc] = pl.qc_Q[qc];
     }
     size_t needA = al(sizeof(int4) * nrows) + 3 * al(sizeof(int) * (nrows + 1)) +
-                   3 * al(sizeof(long long) * (nrows + 1)) + al(sizeof(unsigned long long) * RBIN_N) + 4096;
+                   4 * al(sizeof(long long) * (nrows + 1)) + al(sizeof(unsigned long long) * RBIN_N) + 4096;
     for (int c = 0; c < NPC; ++c) {
         const size_t n = pl.cls[c].size();
         const size_t nb = (n + TB - 1) / TB, nk = (n + TK - 1) / TK, ng = (nk + GROUP - 1) / GROUP;
@@ -906,9 +906,9 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
         launches += 3;
     }
     int4 *d_rows = A.take<int4>(nrows);
-    int *d_cnt = A.take<int>(nrows + 1), *d_cnt32 = A.take<int>(nrows + 1);
+    int *d_cnt = A.take<int>(nrows + 1), *d_cnt32 = A.take<int>(nrows + 1), *d_cntk = A.take<int>(nrows + 1);
     long long *d_off = A.take<long long>(nrows + 1), *d_o64 = A.take<long long>(nrows + 1),
-              *d_o32 = A.take<long long>(nrows + 1);
+              *d_o32 = A.take<long long>(nrows + 1), *d_base = A.take<long long>(nrows + 1);
     unsigned long long *d_hist = A.take<unsigned long long>(RBIN_N);
     ra.rows = d_rows;
     TG_CUDA(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int4) * nrows, cudaMemcpyHostToDevice, st));
@@ -925,7 +925,15 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
     const long long ntl = off[nrows];
     dt.ntiles = ntl;
     if (!ntl) return TG_OK;
+    // start of each row's class in the screened list (the tile shard deals
+    // every class list round-robin from there)
+    std::vector<long long> base(nrows + 1, 0);
+    for (int qc = 0; qc < NQC; ++qc)
+        for (int r = row_qc_begin[qc]; r < row_qc_begin[qc + 1]; ++r) base[r] = off[row_qc_begin[qc]];
+    const bool tshard = opt.shard_mode == TG_SHARD_TILES && opt.nranks > 1;
+    const int srank = tshard ? opt.rank : 0, snr = tshard ? opt.nranks : 1;
     TG_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (nrows + 1), cudaMemcpyHostToDevice, st));
+    TG_CUDA(cudaMemcpyAsync(d_base, base.data(), sizeof(long long) * (nrows + 1), cudaMemcpyHostToDevice, st));
     // ---- phase B buffers: the tiles, their bounds, routing bins, launch lists
     const bool learned = opt.precision == TG_MIXED_LEARNED, bound = opt.precision == TG_MIXED_BOUND;
     size_t needB = 2 * al(sizeof(uint4) * ntl) + al(sizeof(float) * ntl) + al(sizeof(int) * ntl) + 4096;
@@ -982,12 +990,13 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
         bins = d_bin;
     }
     dt.cut = cut;
-    // ---- order-preserving split into the (class, precision) lists
-    k_row_fp32_count<<<gr, 128, 0, st>>>(nrows, d_off, bins, cut, d_cnt32);
+    // ---- order-preserving split of this rank's tiles into the (class, precision) lists
+    k_row_fp32_count<<<gr, 128, 0, st>>>(nrows, d_off, d_base, srank, snr, bins, cut, d_cnt32, d_cntk);
     ++launches;
     TG_CUDA(cudaGetLastError());
-    std::vector<int> c32(nrows);
+    std::vector<int> c32(nrows), ck(nrows);
     TG_CUDA(cudaMemcpyAsync(c32.data(), d_cnt32, sizeof(int) * nrows, cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaMemcpyAsync(ck.data(), d_cntk, sizeof(int) * nrows, cudaMemcpyDeviceToHost, st));
     TG_CUDA(cudaStreamSynchronize(st));
     std::vector<long long> o64(nrows), o32(nrows);
     long long pos = 0;
@@ -995,7 +1004,7 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
         dt.off[2 * qc] = pos;
         for (int r = row_qc_begin[qc]; r < row_qc_begin[qc + 1]; ++r) {
             o64[r] = pos;
-            pos += cnt[r] - c32[r];
+            pos += ck[r] - c32[r];
         }
         dt.off[2 * qc + 1] = pos;
         for (int r = row_qc_begin[qc]; r < row_qc_begin[qc + 1]; ++r) {
@@ -1006,7 +1015,7 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
     dt.off[2 * NQC] = pos;
     TG_CUDA(cudaMemcpyAsync(d_o64, o64.data(), sizeof(long long) * nrows, cudaMemcpyHostToDevice, st));
     TG_CUDA(cudaMemcpyAsync(d_o32, o32.data(), sizeof(long long) * nrows, cudaMemcpyHostToDevice, st));
-    k_row_scatter<<<gr, 128, 0, st>>>(nrows, d_off, d_raw, bins, cut, d_o64, d_o32, d_out);
+    k_row_scatter<<<gr, 128, 0, st>>>(nrows, d_off, d_base, srank, snr, d_raw, bins, cut, d_o64, d_o32, d_out);
     ++launches;
     TG_CUDA(cudaGetLastError());
     // the host vectors must outlive the asynchronous copies
@@ -1264,9 +1273,9 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
     if (stats)
         for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
     const double plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    // (a tile shard is already in the lists)
     rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, nullptr, b->d_boys, pl.G, nullptr, opt.timing != 0, st,
-                     stats, launches, nullptr, opt.kernel_kind, opt.shard_mode == TG_SHARD_TILES ? opt.rank : 0,
-                     opt.shard_mode == TG_SHARD_TILES ? opt.nranks : 1);
+                     stats, launches, nullptr, opt.kernel_kind);
     if (rc != TG_OK) return rc;
     k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, pl.G, d_part, pl.dgrad);
     ++launches;

@@ -187,7 +187,7 @@ __device__ __forceinline__ void pair_table(F *dst, const PrimPairs &pp, int ip, 
 // acc[0..2] += d/dA, acc[3..5] += d/dA + d/dB, acc[6..8] += d/dC (this lane's
 // share; the caller sums the warp).
 template <int LA, int LB, int LC, int LD, typename F>
-__device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, const unsigned *ylist, int ny,
+__device__ void quartet_warp(F *sm, int lane, const F *smallf, const unsigned *zlist, int nz, const unsigned *ylist, int ny,
                              const GeoArgs &geo, const DensArgs &den, const PrimPairs &pp, int sa, int sb, int sc,
                              int sd, int pb0, int nbp, int ib0, int ibs, int pk0, int nkp, double scale,
                              const double *boys, double (&acc)[9])
@@ -232,6 +232,9 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
         gam[it] = (F)g0;
         gam[NAB * NCD + it] = (F)g1;
     }
+    // with one operator the second R tensor stays zero (the sums over both operators read it)
+    if (nops == 1)
+        for (int it = lane; it < NR; it += 32) R[NR + it] = F(0);
     // ket 1-D tables of the first QT ket primitive pairs (kept for every bra primitive)
     const bool ket_once = nkp <= QT;
     if (ket_once)
@@ -398,15 +401,16 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                                 int t, u, v;
                                 herm_tuv(idx, t, u, v);
                                 const F *c = R + op * NR;
+                                // the integer coefficients come from a table (no int-to-float conversion)
                                 if (t > 0) {
                                     val = X * c[hidx(t - 1, u, v)];
-                                    if (t > 1) val += F(t - 1) * c[hidx(t - 2, u, v)];
+                                    if (t > 1) val += smallf[t - 1] * c[hidx(t - 2, u, v)];
                                 } else if (u > 0) {
                                     val = Y * c[hidx(t, u - 1, v)];
-                                    if (u > 1) val += F(u - 1) * c[hidx(t, u - 2, v)];
+                                    if (u > 1) val += smallf[u - 1] * c[hidx(t, u - 2, v)];
                                 } else {
                                     val = Z * c[hidx(t, u, v - 1)];
-                                    if (v > 1) val += F(v - 1) * c[hidx(t, u, v - 2)];
+                                    if (v > 1) val += smallf[v - 1] * c[hidx(t, u, v - 2)];
                                 }
                                 dst = op * NR + idx;
                             }
@@ -448,7 +452,9 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                     cart_xyz(LD, cd % ND, dx, dy, dz);
                     const int nx = cx + dx, ny = cy + dy, nz = cz + dz;
                     const F *e = E3k + cd * NH2;
-                    F w0 = F(0), w1 = F(0);
+                    // fp64: the terms go straight into the lane's W registers;
+                    // fp32: the item's sum is scaled by s^|h1| first
+                    F w0 = FP32 ? F(0) : w0r[k], w1 = FP32 ? F(0) : w1r[k];
                     for (int t2 = 0; t2 <= nx; ++t2)
                         for (int u2 = 0; u2 <= ny; ++u2)
                             for (int v2 = 0; v2 <= nz; ++v2) {
@@ -459,11 +465,12 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                             }
                     if constexpr (FP32) {
                         const F sh = sc_[Lay::SC_POW + t1 + u1 + v1];
-                        w0 *= sh;
-                        w1 *= sh;
+                        w0r[k] += w0 * sh;
+                        w1r[k] += w1 * sh;
+                    } else {
+                        w0r[k] = w0;
+                        w1r[k] = w1;
                     }
-                    w0r[k] += w0;
-                    w1r[k] += w1;
                 }
                 // ---- z[cd][h2] over the derivative boxes of cd, contracted with dE^{cd}/dC
                 {
@@ -482,7 +489,8 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                         const bool gx = t2 <= nx + 1 && iny && inz, gy = inx && u2 <= ny + 1 && inz,
                                    gz = inx && iny && v2 <= nz + 1;
                         const F *f0 = Fr + cd * NH1, *f1 = Fr + NCD * NH1 + cd * NH1;
-                        F z0 = F(0), z1 = F(0);
+                        // both operators in one sum (with one operator, F_1 and R_1 are zero)
+                        F z = F(0);
 #pragma unroll
                         for (int t1 = 0; t1 <= L1; ++t1)
 #pragma unroll
@@ -492,14 +500,12 @@ __device__ void quartet_warp(F *sm, int lane, const unsigned *zlist, int nz, con
                                     const int r = hidx(t1 + t2, u1 + u2, v1 + v2);
                                     if constexpr (FP32) {
                                         const F sh = sc_[Lay::SC_POW + t1 + u1 + v1];
-                                        z0 += f0[hidx(t1, u1, v1)] * sh * R0[r];
-                                        z1 += f1[hidx(t1, u1, v1)] * sh * R1[r];
+                                        z += (f0[hidx(t1, u1, v1)] * R0[r] + f1[hidx(t1, u1, v1)] * R1[r]) * sh;
                                     } else {
-                                        z0 += f0[hidx(t1, u1, v1)] * R0[r];
-                                        z1 += f1[hidx(t1, u1, v1)] * R1[r];
+                                        z += f0[hidx(t1, u1, v1)] * R0[r];
+                                        z += f1[hidx(t1, u1, v1)] * R1[r];
                                     }
                                 }
-                        F z = z0 + (nops == 2 ? z1 : F(0));
                         const int n2 = t2 + u2 + v2;
                         if constexpr (FP32) z *= sc_[Lay::SC_POW + n2];
                         z = flip_if(z, n2);
@@ -621,6 +627,8 @@ __global__ void __launch_bounds__(TILE, 2) k_grad_warp(const MolDesc *__restrict
     // item lists: (cd, h2) with h2 in a derivative box of cd, (ab, h1) likewise;
     // packed as pair | t << 8 | u << 12 | v << 16 | hermite index << 20
     __shared__ int nlist[2];
+    __shared__ F smallf[16];  // 0, 1, ..., 15 as F
+    if (threadIdx.x < 16) smallf[threadIdx.x] = F(threadIdx.x);
     if (threadIdx.x == 0) {
         int n = 0;
         for (int cd = 0; cd < Lay::NCD; ++cd)
@@ -711,7 +719,7 @@ __global__ void __launch_bounds__(TILE, 2) k_grad_warp(const MolDesc *__restrict
                 double acc[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) acc[k] = 0.0;
-                quartet_warp<LA, LB, LC, LD, F>(wsm, lane, zlist, nz, ylist, ny, geo, md.den, pp, sa, sb, sc, sd,
+                quartet_warp<LA, LB, LC, LD, F>(wsm, lane, smallf, zlist, nz, ylist, ny, geo, md.den, pp, sa, sb, sc, sd,
                                                 bra.poff[bi], nbp, split, S, ket.poff[ki], nkp, scale, boys, acc);
 #pragma unroll
                 for (int k = 0; k < 9; ++k)

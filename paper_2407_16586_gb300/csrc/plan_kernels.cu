@@ -125,29 +125,46 @@ __global__ void k_route_bins(long long n, const uint4 *__restrict__ tiles, const
     atomicAdd(hist + b, 1ull);
 }
 
-// fp32 tiles of each row: tiles whose bin is below the cut-off
-// (bin == nullptr: every tile counts as bin 0, so cut 0 routes all to fp64
-// and any cut > 0 all to fp32)
-__global__ void k_row_fp32_count(int nrows, const long long *__restrict__ off, const int *__restrict__ bin, int cut,
-                                 int *cnt32)
+// Tile shard (tg_options.shard_mode = TG_SHARD_TILES): tile i of the screened
+// list belongs to rank (i - base of its class) mod snr, i.e. the class lists
+// are dealt round-robin in their planner order BEFORE the fp32 / fp64 split,
+// so a shard holds the same tiles at every precision and the route is the
+// one of the whole list.
+__device__ __forceinline__ bool in_shard(long long i, long long base, int srank, int snr)
+{
+    return snr <= 1 || (i - base) % snr == srank;
+}
+
+// Kept tiles of each row (cntk) and those of them routed to fp32 (cnt32): a
+// tile goes to fp32 iff its bin is below the cut-off (bin == nullptr: every
+// tile counts as bin 0, so cut 0 routes all to fp64 and any cut > 0 all to
+// fp32).
+__global__ void k_row_fp32_count(int nrows, const long long *__restrict__ off, const long long *__restrict__ base,
+                                 int srank, int snr, const int *__restrict__ bin, int cut, int *cnt32, int *cntk)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
-    int c = 0;
-    for (long long i = off[r]; i < off[r + 1]; ++i) c += ((bin ? bin[i] : 0) < cut) ? 1 : 0;
+    int c = 0, k = 0;
+    for (long long i = off[r]; i < off[r + 1]; ++i) {
+        if (!in_shard(i, base[r], srank, snr)) continue;
+        ++k;
+        c += ((bin ? bin[i] : 0) < cut) ? 1 : 0;
+    }
     cnt32[r] = c;
+    cntk[r] = k;
 }
 
-// Row r's tiles, in order, to its fp64 slots at o64[r] and its fp32 slots at
-// o32[r] of the launch list (molecule 0, bra tile, ket tile, 0).
-__global__ void k_row_scatter(int nrows, const long long *__restrict__ off, const uint4 *__restrict__ tiles,
-                              const int *__restrict__ bin, int cut, const long long *__restrict__ o64,
-                              const long long *__restrict__ o32, uint4 *out)
+// Row r's kept tiles, in order, to its fp64 slots at o64[r] and its fp32
+// slots at o32[r] of the launch list (molecule 0, bra tile, ket tile, 0).
+__global__ void k_row_scatter(int nrows, const long long *__restrict__ off, const long long *__restrict__ base,
+                              int srank, int snr, const uint4 *__restrict__ tiles, const int *__restrict__ bin, int cut,
+                              const long long *__restrict__ o64, const long long *__restrict__ o32, uint4 *out)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     long long a = o64[r], b = o32[r];
     for (long long i = off[r]; i < off[r + 1]; ++i) {
+        if (!in_shard(i, base[r], srank, snr)) continue;
         const uint4 t = tiles[i];
         const bool f32 = (bin ? bin[i] : 0) < cut;
         out[f32 ? b++ : a++] = make_uint4(0u, t.y, t.z, 0u);

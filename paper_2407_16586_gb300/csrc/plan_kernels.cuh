@@ -48,8 +48,10 @@ __global__ void k_tile_rows(RowArgs a, int mode, int *count, const long long *of
 __global__ void k_tile_refs(long long n, const uint4 *tiles, RowArgs a, TileRef *refs);
 __global__ void k_route_bins(long long n, const uint4 *tiles, const float *val, int kind, double c0, double c1,
                              RowArgs a, int *bin, unsigned long long *hist);
-__global__ void k_row_fp32_count(int nrows, const long long *off, const int *bin, int cut, int *cnt32);
-__global__ void k_row_scatter(int nrows, const long long *off, const uint4 *tiles, const int *bin, int cut,
-                              const long long *o64, const long long *o32, uint4 *out);
+__global__ void k_row_fp32_count(int nrows, const long long *off, const long long *base, int srank, int snr,
+                                 const int *bin, int cut, int *cnt32, int *cntk);
+__global__ void k_row_scatter(int nrows, const long long *off, const long long *base, int srank, int snr,
+                              const uint4 *tiles, const int *bin, int cut, const long long *o64, const long long *o32,
+                              uint4 *out);
 
 }  // namespace tg

@@ -265,6 +265,28 @@ def test_tile_shards_sum_to_the_whole(tg):
     assert np.abs(tot - whole).max() <= 1e-12
 
 
+def test_tile_shards_hold_the_same_tiles_at_every_precision(tg):
+    """The tile shard is dealt before the fp32 / fp64 split and the route is the
+    whole call's: a rank's mixed partial covers the same quartets as its fp64
+    partial and stays within the whole call's mixed_tol of it, and the ranks'
+    fp32 quartets add up to the whole call's."""
+    s = synth.molecule(19, 3, 3)
+    b = tg.Basis(s)
+    tol = 1e-7
+    _, stw = b.grad2e(s["pairs"], screen_tol=1e-10, precision=tg.TG_MIXED_BOUND, mixed_tol=tol)
+    assert 0 < stw["fp32_quartets"] < stw["quartets"]
+    n32 = 0
+    for r in range(3):
+        kw = dict(screen_tol=1e-10, rank=r, nranks=3, shard_mode=tg.TG_SHARD_TILES)
+        g64, s64 = b.grad2e(s["pairs"], **kw)
+        gm, sm = b.grad2e(s["pairs"], precision=tg.TG_MIXED_BOUND, mixed_tol=tol, **kw)
+        assert sm["quartets"] == s64["quartets"]
+        assert sm["prim_quartets"] == s64["prim_quartets"]
+        assert np.abs(gm - g64).max() <= tol
+        n32 += sm["fp32_quartets"]
+    assert n32 == stw["fp32_quartets"]
+
+
 def test_allocation_failure_leaves_the_output_untouched(tg, monkeypatch):
     """With the host-side hook TDGRAD_FAIL_ALLOC=1 every growth of the work
     areas fails as an out-of-memory would: the call returns TG_ENOMEM and the
