@@ -131,7 +131,9 @@ def aggregate_over_ranks(dist, ms, units, device):
 
 def workload(name):
     """The timed system: "c2" (the default, the 32-atom chain), "c1" (6 atoms),
-    "c4" (the 300-atom core + water cluster, 2790 basis functions), or
+    "c4" (the 300-atom core + water cluster, 2790 basis functions), "c5"
+    (the 1500-atom core + water shells, 13950 basis functions, screened at
+    1e-12), or
     "chain:SEED:NHEAVY:NH" (a smaller chain of the same recipe, used for
     profiler captures)."""
     from paper_2407_16586_gb300 import synth
@@ -142,6 +144,9 @@ def workload(name):
     if name == "c4":
         return synth.config(3), ("c4: 300-atom core + water cluster, 2790 bf, 3 density pairs, wB97X-like, "
                                  "tau=1e-10")
+    if name == "c5":
+        return synth.config(4), ("c5: 1500-atom core + water shells, 13950 bf, 3 density pairs, wB97X-like, "
+                                 "tau=1e-12")
     parts = name.split(":")
     if len(parts) == 4 and parts[0] == "chain":
         seed, nheavy, nh = (int(x) for x in parts[1:])
@@ -322,7 +327,8 @@ def run_c3(args, prec, router, torch):
 
 
 def run_large(args, prec, router, torch):
-    """The 300-atom c4 cluster: one step takes many minutes, so the kernels are
+    """The c4 (300-atom) and c5 (1500-atom) clusters: one step takes many
+    minutes (c4) or days (c5, about 4 x 10^11 quartets), so the kernels are
     warmed on c1, then ONE mixed step and ONE fp64 step are timed (CUDA events
     on the launching stream, per-class events on), and the fp64 gradient is
     the reference of the mixed one.  With --shard N both steps evaluate the
@@ -342,8 +348,12 @@ def run_large(args, prec, router, torch):
     b1 = tg.Basis(c1)
     for _ in range(2):
         b1.grad2e(c1["pairs"], screen_tol=TAU, precision=prec, router=router)
+    t0 = time.perf_counter()
     s, wname = workload(args.workload)
+    t1 = time.perf_counter()
+    tau = 1e-12 if args.workload == "c5" else TAU
     basis = tg.Basis(s)
+    t2 = time.perf_counter()
     dpairs = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev), cj, ck, cl, om)
               for (a, b, cj, ck, cl, om) in s["pairs"]]
     gout = torch.empty((s["natom"], 3), dtype=torch.float64, device=dev)
@@ -356,7 +366,7 @@ def run_large(args, prec, router, torch):
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=True,
+        _, st = basis.grad2e(dpairs, screen_tol=tau, precision=precision, router=router, out=gout, timing=True,
                              **shard)
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -367,18 +377,21 @@ def run_large(args, prec, router, torch):
     th.start()
     time.sleep(0.3)
     ms, st, g = one(prec)
+    free, total = torch.cuda.mem_get_info(dev)  # the library's work areas are sized by this call's plan
     ms64, st64, g64 = (ms, st, g) if prec == tg.TG_FP64 else one(tg.TG_FP64)
     stop.set()
     th.join(timeout=2)
     line = {"metric": METRIC, "value": st["quartets"] / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64", "data": "synthetic",
-            "config": {"workload": wname, "precision": args.precision, "screen_tol": TAU, "mixed_tol": 1e-6,
+            "config": {"workload": wname, "precision": args.precision, "screen_tol": tau, "mixed_tol": 1e-6,
                        "quartets_per_step": st["quartets"], "fp32_quartets_per_step": st["fp32_quartets"],
                        "prim_quartets_per_step": st["prim_quartets"], "pairs": st["pairs"], "tiles": st["tiles"],
                        "warm-up": "two c1 calls (kernels and context loaded); one timed step per precision",
                        "shard": ("tile-cyclic shard 0 of %d" % nsh) if nsh > 1 else "whole gradient",
                        "full_gradient_s_estimate": {"mixed": nsh * ms / 1e3, "fp64": nsh * ms64 / 1e3},
+                       "device_memory_in_use_gb": round((total - free) / 1e9, 2),
+                       "host_generate_s": round(t1 - t0, 1), "basis_create_s": round(t2 - t1, 1),
                        "l2": "flushed (512 MB write) before each timed step"},
             "e2e": None, "gpu_launches": st["launches"], "plan_ms": st["plan_ms"],
             "roofline": roofline_entry(st), "clocks": _clocks_summary(rows, 0),
@@ -438,19 +451,19 @@ def main():
     ap.add_argument("--router", default=os.path.join(ROOT, "paper_2407_16586_gb300", "data", "router.bin"))
     ap.add_argument("--ref-shards", type=int, default=None, help="oracle shards (default 600; 50000 for c4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", help='c2 (default), c1, c3, c3:N, c4, or chain:SEED:NHEAVY:NH')
+    ap.add_argument("--workload", default="c2", help='c2 (default), c1, c3, c3:N, c4, c5 or chain:SEED:NHEAVY:NH')
     ap.add_argument("--bound-steps", type=int, default=1, help="timed mixed-bound steps for the comparison (0: skip)")
     ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
     ap.add_argument("--fock", action="store_true", help="time the Fock-type build (tg_fock2e) instead")
-    ap.add_argument("--shard", type=int, default=1, help="c4: time tile-cyclic shard 0 of this many")
+    ap.add_argument("--shard", type=int, default=1, help="c4, c5: time tile-cyclic shard 0 of this many")
     args = ap.parse_args()
     if args.opcount:
         print_opcount()
         return 0
     # c4 steps take minutes each: one warm-up step (the default c2 line keeps >= 3)
-    args.warmup = max(args.warmup, 1 if args.workload == "c4" or args.workload.startswith("c3") else 3)
+    args.warmup = max(args.warmup, 1 if args.workload in ("c4", "c5") or args.workload.startswith("c3") else 3)
     if args.ref_shards is None:
-        args.ref_shards = 50000 if args.workload == "c4" else 600
+        args.ref_shards = {"c4": 50000, "c5": 2000000}.get(args.workload, 600)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -480,7 +493,7 @@ def main():
         return run_fock(args, torch)
     if args.workload.startswith("c3"):
         return run_c3(args, prec, router, torch)
-    if args.workload == "c4":
+    if args.workload in ("c4", "c5"):
         return run_large(args, prec, router, torch)
     s, wname = workload(args.workload)
     basis = tg.Basis(s)

@@ -237,9 +237,11 @@ int tg_fock2e(const tg_basis *b, int npair, const tg_fpair *pairs, const tg_opti
  * device_ptrs the densities are read from the caller's device buffers at
  * every run (their contents may change, the plan does not), otherwise they
  * are copied at creation.  opt->autotune = 1 autotunes every class list
- * on a sample of its tiles: the kernel form (thread, group or warp), the
- * persistent grid (1, 2 or 4 CTAs per SM) and the work-unit shape (bra
- * primitive splits per tile: automatic, 1 or 4), keeping the fastest.
+ * on its costliest 2 x (SM count) tiles: the kernel form (thread, group or
+ * warp), the persistent grid (1, 2 or 4 CTAs per SM) and the work-unit shape
+ * (bra primitive splits per tile: automatic, 1 or 4), searched one
+ * coordinate at a time (form, then grid, then splits; 7 timed launches per
+ * list), keeping the fastest.
  * tg_batch_run replays the graph on opt->stream and writes grads[m]
  * (natom_m * 3, host unless device_ptrs).  Not part of the paper, which
  * evaluates one system at a time (Sec. II.C). */

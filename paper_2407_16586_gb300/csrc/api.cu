@@ -934,20 +934,29 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
     const int srank = tshard ? opt.rank : 0, snr = tshard ? opt.nranks : 1;
     TG_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (nrows + 1), cudaMemcpyHostToDevice, st));
     TG_CUDA(cudaMemcpyAsync(d_base, base.data(), sizeof(long long) * (nrows + 1), cudaMemcpyHostToDevice, st));
-    // ---- phase B buffers: the tiles, their bounds, routing bins, launch lists
+    // ---- phase B buffers: the tiles, their bounds and routing bins (24 B per
+    // screened tile), this rank's launch lists (16 B per tile of the shard) and,
+    // for the learned router, feature and prediction buffers for one chunk of
+    // at most RCHUNK tiles at a time
     const bool learned = opt.precision == TG_MIXED_LEARNED, bound = opt.precision == TG_MIXED_BOUND;
-    size_t needB = 2 * al(sizeof(uint4) * ntl) + al(sizeof(float) * ntl) + al(sizeof(int) * ntl) + 4096;
-    if (learned) needB += al(sizeof(TileRef) * ntl) + al(sizeof(float) * ntl * NFEAT) + al(sizeof(float) * ntl);
+    constexpr long long RCHUNK = 1LL << 25;
+    const long long nout = snr > 1 ? std::min(ntl, ntl / snr + 2 * NQC) : ntl;  // a class list of n deals <= n/snr + 1
+    const long long nch = std::min(ntl, RCHUNK);
+    size_t needB = al(sizeof(uint4) * ntl) + al(sizeof(uint4) * nout) + al(sizeof(float) * ntl) +
+                   al(sizeof(int) * ntl) + 4096;
+    if (learned) needB += al(sizeof(TileRef) * nch) + al(sizeof(float) * nch * NFEAT) + al(sizeof(float) * nch);
     DevArena &B = b->ws4;
     TG_CUDA(B.reserve(needB));
     B.used = 0;
-    uint4 *d_raw = B.take<uint4>(ntl), *d_out = B.take<uint4>(ntl);
+    uint4 *d_raw = B.take<uint4>(ntl), *d_out = B.take<uint4>(nout);
     float *d_bnd = B.take<float>(ntl);
     int *d_bin = B.take<int>(ntl);
     k_tile_rows<<<gr, 128, 0, st>>>(ra, 1, nullptr, d_off, d_raw, d_bnd);
     ++launches;
     TG_CUDA(cudaGetLastError());
-    const unsigned gt = (unsigned)((ntl + 127) / 128);
+    // grid-stride routing-bin launches: a few blocks per SM, each with its own histogram
+    const unsigned gbin = (unsigned)std::max<long long>(1, std::min<long long>((ntl + 127) / 128, 8LL * b->nsm));
+    const size_t hbytes = sizeof(unsigned int) * RBIN_N;
     int cut = 0;
     const int *bins = nullptr;
     if (opt.precision == TG_FP32) {
@@ -955,24 +964,29 @@ int device_tiles(tg_basis *b, const Plan &pl, const tg_options &opt, cudaStream_
     } else if (bound || learned) {
         TG_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * RBIN_N, st));
         if (bound) {
-            k_route_bins<<<gt, 128, 0, st>>>(ntl, d_raw, d_bnd, 0, kEps32Bound * TILE, 0.0, ra, d_bin, d_hist);
+            k_route_bins<<<gbin, 128, hbytes, st>>>(ntl, d_raw, d_bnd, 0, kEps32Bound * TILE, 0.0, ra, d_bin, d_hist);
             ++launches;
         } else {
-            TileRef *d_ref = B.take<TileRef>(ntl);
-            float *d_feat = B.take<float>(ntl * NFEAT), *d_pred = B.take<float>(ntl);
-            k_tile_refs<<<gt, 128, 0, st>>>(ntl, d_raw, ra, d_ref);
-            k_tile_features<<<gt, 128, 0, st>>>((int)ntl, d_ref, feature_args(b, pl), d_feat);
+            TileRef *d_ref = B.take<TileRef>(nch);
+            float *d_feat = B.take<float>(nch * NFEAT), *d_pred = B.take<float>(nch);
             const tg_router *r = opt.router;
             float *dparams = b->d_router;
             TG_CUDA(cudaMemcpyAsync(dparams, r->params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, st));
             TG_CUDA(cudaMemcpyAsync(dparams + NPARAM, r->mu, sizeof(float) * NFEAT, cudaMemcpyHostToDevice, st));
             TG_CUDA(cudaMemcpyAsync(dparams + NPARAM + NFEAT, r->sd, sizeof(float) * NFEAT, cudaMemcpyHostToDevice,
                                     st));
-            k_mlp_predict<<<gt, 128, 0, st>>>((int)ntl, d_feat, dparams + NPARAM, dparams + NPARAM + NFEAT, dparams,
-                                             d_pred);
-            k_route_bins<<<gt, 128, 0, st>>>(ntl, d_raw, d_pred, 1, (double)r->eps_rel, (double)r->margin, ra, d_bin,
-                                             d_hist);
-            launches += 4;
+            for (long long c0 = 0; c0 < ntl; c0 += RCHUNK) {
+                const long long n = std::min(RCHUNK, ntl - c0);
+                const unsigned g = (unsigned)((n + 127) / 128);
+                const unsigned gb = (unsigned)std::min<long long>(g, 8LL * b->nsm);
+                k_tile_refs<<<g, 128, 0, st>>>(n, d_raw + c0, ra, d_ref);
+                k_tile_features<<<g, 128, 0, st>>>((int)n, d_ref, feature_args(b, pl), d_feat);
+                k_mlp_predict<<<g, 128, 0, st>>>((int)n, d_feat, dparams + NPARAM, dparams + NPARAM + NFEAT, dparams,
+                                                 d_pred);
+                k_route_bins<<<gb, 128, hbytes, st>>>(n, d_raw + c0, d_pred, 1, (double)r->eps_rel,
+                                                      (double)r->margin, ra, d_bin + c0, d_hist);
+                launches += 4;
+            }
         }
         TG_CUDA(cudaGetLastError());
         std::vector<unsigned long long> hist(RBIN_N);
@@ -1603,10 +1617,14 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
                            cudaMemcpyHostToDevice));
     const double *boys = bt->bases[0]->d_boys;
 
-    // ---- autotune every (class, precision) list on a sample of its tiles:
-    // kernel form (thread, group, warp), grid capped at 1, 2 or 4 CTAs per SM,
-    // and unit shape (bra-primitive splits per tile: automatic, 1 or 4); the
-    // fastest combination is kept
+    // ---- autotune every (class, precision) list on a sample of its first
+    // tiles (the costliest: the lists are sorted by decreasing cost): kernel
+    // form (thread, group, warp), grid capped at 1, 2 or 4 CTAs per SM, and
+    // unit shape (bra-primitive splits per tile: automatic, 1 or 4), searched
+    // one coordinate at a time from (default form, 2 CTAs per SM, automatic
+    // splits): the fastest form, then the fastest grid cap for it, then the
+    // fastest split -- 7 timed launches per list instead of the 27 of the
+    // full product
     bt->grids.assign(2 * NQC, G);
     bt->kinds.assign(2 * NQC, opt.kernel_kind);
     bt->splits.assign(2 * NQC, 0);
@@ -1621,30 +1639,44 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
             Exec sub;
             sub.natom_total = natom_total;
             sub.natom_max = natom_max;
-            const long long ns = std::min<long long>(nt, 8LL * nsm);
+            const long long ns = std::min<long long>(nt, 2LL * nsm);
             for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : ns;
+            auto time_cfg = [&](int kind, int mult, int split, float &ms) -> int {
+                std::vector<int> gr(2 * NQC, mult * nsm), kd(2 * NQC, kind), sp(2 * NQC, split);
+                int dummy = 0;
+                cudaEventRecord(e0, st);
+                int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt, nullptr,
+                                     boys, G, gr.data(), false, st, nullptr, dummy, kd.data(), 0, 0, 1, sp.data());
+                cudaEventRecord(e1, st);
+                if (rc != TG_OK) return rc;
+                TG_CUDA(cudaEventSynchronize(e1));
+                ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                return TG_OK;
+            };
+            int bk = 0, bm = 2, bs = 0;
             float best = -1.f;
-            for (int kind = 1; kind <= 3; ++kind)
-                for (int mult : {1, 2, 4})
-                    for (int split : {0, 1, 4}) {
-                    std::vector<int> gr(2 * NQC, mult * nsm), kd(2 * NQC, kind), sp(2 * NQC, split);
-                    int dummy = 0;
-                    cudaEventRecord(e0, st);
-                    int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt,
-                                         nullptr, boys, G, gr.data(), false, st, nullptr, dummy, kd.data(), 0, 0, 1,
-                                         sp.data());
-                    cudaEventRecord(e1, st);
-                    if (rc != TG_OK) return rc;
-                    TG_CUDA(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (best < 0.f || ms < best) {
-                        best = ms;
-                        bt->grids[k] = mult * nsm;
-                        bt->kinds[k] = kind;
-                        bt->splits[k] = split;
-                    }
-                    }
+            for (int kind = 1; kind <= 3; ++kind) {
+                float ms;
+                const int rc = time_cfg(kind, bm, bs, ms);
+                if (rc != TG_OK) return rc;
+                if (best < 0.f || ms < best) best = ms, bk = kind;
+            }
+            for (int mult : {1, 4}) {
+                float ms;
+                const int rc = time_cfg(bk, mult, bs, ms);
+                if (rc != TG_OK) return rc;
+                if (ms < best) best = ms, bm = mult;
+            }
+            for (int split : {1, 4}) {
+                float ms;
+                const int rc = time_cfg(bk, bm, split, ms);
+                if (rc != TG_OK) return rc;
+                if (ms < best) best = ms, bs = split;
+            }
+            bt->grids[k] = bm * nsm;
+            bt->kinds[k] = bk;
+            bt->splits[k] = bs;
         }
         bt->G = G = std::max(G, *std::max_element(bt->grids.begin(), bt->grids.end()));
     }

@@ -105,24 +105,33 @@ __global__ void k_tile_refs(long long n, const uint4 *__restrict__ tiles, RowArg
 
 // Log-binned fp32 error estimate of every tile (see route_bin) and the
 // count of tiles per bin.  kind 0: e = c0 * nfq(class) * bound; kind 1:
-// e = c0 * 10^(prediction + c1).
+// e = c0 * 10^(prediction + c1).  Grid-stride with a per-block histogram in
+// shared memory (32-bit counts, at most 2^31 tiles per launch), added to the
+// global one bin by bin at the end, so the global atomics do not pile up on
+// the few bins that hold most tiles.
 __global__ void k_route_bins(long long n, const uint4 *__restrict__ tiles, const float *__restrict__ val, int kind,
                              double c0, double c1, RowArgs a, int *bin, unsigned long long *hist)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double e;
-    if (kind == 0) {
-        const int qc = tiles[i].w;
-        const int P = a.qcP[qc], Q = a.qcQ[qc];
-        const int nfq = ncart(pc_la(P)) * ncart(pc_lb(P)) * ncart(pc_la(Q)) * ncart(pc_lb(Q));
-        e = c0 * nfq * (double)val[i];
-    } else {
-        e = c0 * pow(10.0, (double)val[i] + c1);
+    extern __shared__ unsigned int sh_hist[];
+    for (int k = threadIdx.x; k < RBIN_N; k += blockDim.x) sh_hist[k] = 0u;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double e;
+        if (kind == 0) {
+            const int qc = tiles[i].w;
+            const int P = a.qcP[qc], Q = a.qcQ[qc];
+            const int nfq = ncart(pc_la(P)) * ncart(pc_lb(P)) * ncart(pc_la(Q)) * ncart(pc_lb(Q));
+            e = c0 * nfq * (double)val[i];
+        } else {
+            e = c0 * pow(10.0, (double)val[i] + c1);
+        }
+        const int b = route_bin(e);
+        bin[i] = b;
+        atomicAdd(sh_hist + b, 1u);
     }
-    const int b = route_bin(e);
-    bin[i] = b;
-    atomicAdd(hist + b, 1ull);
+    __syncthreads();
+    for (int k = threadIdx.x; k < RBIN_N; k += blockDim.x)
+        if (sh_hist[k]) atomicAdd(hist + k, (unsigned long long)sh_hist[k]);
 }
 
 // Tile shard (tg_options.shard_mode = TG_SHARD_TILES): tile i of the screened
