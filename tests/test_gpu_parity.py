@@ -270,9 +270,9 @@ def test_tile_shards_hold_the_same_tiles_at_every_precision(tg):
     whole call's: a rank's mixed partial covers the same quartets as its fp64
     partial and stays within the whole call's mixed_tol of it, and the ranks'
     fp32 quartets add up to the whole call's."""
-    s = synth.molecule(19, 3, 3)
+    s = synth.molecule(18, 4, 4)
     b = tg.Basis(s)
-    tol = 1e-7
+    tol = 1e-6
     _, stw = b.grad2e(s["pairs"], screen_tol=1e-10, precision=tg.TG_MIXED_BOUND, mixed_tol=tol)
     assert 0 < stw["fp32_quartets"] < stw["quartets"]
     n32 = 0
