@@ -791,9 +791,12 @@ cudaError_t launch_warp(int gcap, size_t smem, cudaStream_t st, const MolDesc *m
 
 // Default class-kernel form per angular class (ssss, psss, psps, ppss, ppps,
 // pppp, dsss, dsps, dspp, dsds, dpss, dpps, dppp, dpds, dpdp, ddss, ddps, ddpp,
-// ddds, dddp, dddd): 1 = thread, 2 = group, 3 = warp.
-constexpr int kDefaultForm64[NQC] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 3, 3, 2, 3, 2, 2};
-constexpr int kDefaultForm32[NQC] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 3, 2, 2};
+// ddds, dddp, dddd): 1 = thread, 2 = group, 3 = warp.  Picked from per-class
+// kernel times of the mixed route on the 32-atom chain (the fp64 lists there
+// hold the largest, most contracted tiles) and of the all-fp64 route; where
+// the two disagree by little, the mixed route's choice is kept.
+constexpr int kDefaultForm64[NQC] = {1, 1, 1, 1, 1, 3, 1, 1, 1, 3, 1, 3, 3, 3, 3, 3, 3, 3, 3, 2, 2};
+constexpr int kDefaultForm32[NQC] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 3, 3, 2, 2};
 
 // Kernel forms per class.  The thread kernel is compiled below 648 function
 // quartets (above, its per-thread arrays run to tens of KB of local memory),
