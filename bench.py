@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--bound-steps", type=int, default=1, help="timed mixed-bound steps for the comparison (0: skip)")
     ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
     ap.add_argument("--fock", action="store_true", help="time the Fock-type build (tg_fock2e) instead")
+    ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
+                    help="1: tg_options.autotune = 1 (launches tuned per class list on the first warm-up call)")
     ap.add_argument("--shard", type=int, default=1, help="c4, c5: time tile-cyclic shard 0 of this many")
     args = ap.parse_args()
     if args.opcount:
@@ -515,7 +517,7 @@ def main():
 
     def step(precision, timing=False):
         _, st = basis.grad2e(dpairs, screen_tol=TAU, precision=precision, router=router, out=gout, timing=timing,
-                             **shard)
+                             autotune=args.autotune, **shard)
         if dist:
             dist.all_reduce(gout)
         return st
@@ -565,7 +567,7 @@ def main():
         torch.cuda.synchronize(dev)
         t = time.perf_counter()
         _, st = basis.grad2e(hpairs, screen_tol=TAU, precision=prec, router=router, out=hout,
-                             stream=stream.cuda_stream, **shard)
+                             stream=stream.cuda_stream, autotune=args.autotune, **shard)
         if dist:
             hg = torch.from_numpy(hout).to(dev)
             dist.all_reduce(hg)
@@ -605,6 +607,8 @@ def main():
                        "quartets_per_step": st0["quartets"], "fp32_quartets_per_step": st0["fp32_quartets"],
                        "prim_quartets_per_step": st0["prim_quartets"], "pairs": st0["pairs"], "tiles": st0["tiles"],
                        "l2": "flushed (512 MB write) before each timed step",
+                       "autotune": ("launches tuned per class list on the first warm-up call, reused"
+                                    if args.autotune else "per-class default kernel forms"),
                        "parallelism": ("one gradient, tile-cyclic shards per rank, NCCL all-reduce of natom x 3"
                                        if world > 1 else "single GPU")},
             "e2e": {"value": e2e_q / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,

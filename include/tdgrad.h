@@ -111,7 +111,14 @@ typedef struct {
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
     int rank, nranks;       /* shard; default 0 / 1 */
     int timing;             /* 1: time every class kernel with CUDA events (tg_stats.class_ms) */
-    int autotune;           /* tg_batch_create only, 1: autotune every class list (see there) */
+    int autotune;           /* 0 (default): the per-class default kernel forms and grids.
+                               tg_batch_create: 1 autotunes every class list (see there).
+                               tg_grad2e: 1 tunes every (class, precision) list the same way
+                               on the basis's first call with autotune = 1 and reuses the
+                               choices on later calls (a list empty at that call keeps the
+                               defaults); 2 tunes again on this call.  The tuning launches
+                               time sample tiles and do not change the result's definition:
+                               every form computes the same quartets in the same precision. */
     int kernel_kind;        /* TG_KERNEL_DEFAULT (default), _THREAD, _GROUP or _WARP */
     int deterministic;      /* 1 (default): fixed-order fp64 sums, bitwise reproducible on one
                                device for one launch configuration.  Every path of this

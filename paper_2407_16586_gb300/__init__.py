@@ -291,14 +291,17 @@ class Basis:
         return F, st.as_dict()
 
     def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
-               timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0, shard_mode=0):
+               timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0, shard_mode=0, autotune=0):
         """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
         torch CUDA tensors (then the densities and ``out`` stay on the device).  ``kernel``
         picks the class kernels: 0 per-class default, 1 one quartet per thread, 2 a thread
-        group per quartet where compiled.  ``class_mask`` (0 = all) keeps the angular
-        classes whose bits are set."""
+        group per quartet where compiled, 3 a warp per quartet where compiled.  ``class_mask``
+        (0 = all) keeps the angular classes whose bits are set.  ``autotune`` 1 tunes the
+        launches of every class list on this basis's first such call and reuses them, 2
+        tunes again (tg_options.autotune)."""
         opt = tg_options_default()
         opt.kernel_kind = int(kernel)
+        opt.autotune = int(autotune)
         opt.class_mask = int(class_mask)
         opt.shard_mode = int(shard_mode)
         opt.screen_tol = float(screen_tol)

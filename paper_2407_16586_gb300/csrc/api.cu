@@ -88,6 +88,11 @@ struct tg_basis {
     DevArena ws5;       // Fock build: densities, combined matrices, F
     float *d_router = nullptr;  // router parameters, mean and std on the device
     int nsm = 0;
+    // tg_grad2e's autotuner (tg_options.autotune = 1): kernel form, grid cap
+    // and bra-primitive splits per (class, precision) list, chosen on the
+    // first such call and kept for the later ones
+    bool tuned = false;
+    int tune_kind[2 * NQC], tune_grid[2 * NQC], tune_split[2 * NQC];
 };
 
 namespace {
@@ -387,6 +392,7 @@ int check_pairs(int npair, const tg_pair *pairs, const tg_options &opt, double &
     for (int r : opt.reserved)
         if (r != 0) return TG_EINVAL;
     if (opt.shard_mode != TG_SHARD_PAIR_KEY && opt.shard_mode != TG_SHARD_TILES) return TG_EINVAL;
+    if (opt.autotune < 0 || opt.autotune > 2) return TG_EINVAL;
     omega = 0.0;
     use_lr = 0;
     for (int p = 0; p < npair; ++p) {
@@ -1185,6 +1191,73 @@ void alu_peaks(double &p64, double &p32)
     p32 = (double)nsm * 128.0 * 2.0 * khz * 1e3;
 }
 
+// Autotuner of the class launches: for every (class, precision) list of ex
+// with more than nsm tiles, time its costliest 2 x nsm tiles (the lists are
+// sorted by decreasing cost) and search the kernel form (thread, group,
+// warp), the grid cap (1, 2 or 4 CTAs per SM) and the unit shape (bra
+// primitive splits per tile: automatic, 1 or 4) one coordinate at a time
+// from (form 1, 2 CTAs per SM, automatic splits): the
+// fastest form, then the fastest grid cap for it, then the fastest split
+// (7 timed launches per list).  Lists left untimed keep kinds[k] = 0 (the
+// default form), grids[k] = 0 (the persistent grid) and splits[k] = 0.
+// The sample launches write into d_part and d_cnt, which the caller clears
+// afterwards.
+int tune_lists(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, double *d_part,
+               unsigned long long *d_cnt, const double *boys, int G, int nsm, cudaStream_t st, int *kinds,
+               int *grids, int *splits)
+{
+    for (int k = 0; k < 2 * NQC; ++k) kinds[k] = grids[k] = splits[k] = 0;
+    EventPair ev;
+    TG_CUDA(ev.create());
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
+    for (int k = 0; k < 2 * NQC; ++k) {
+        const long long nt = ex.off[k + 1] - ex.off[k];
+        if (nt <= nsm) continue;
+        Exec sub;
+        sub.natom_total = ex.natom_total;
+        sub.natom_max = ex.natom_max;
+        const long long ns = std::min<long long>(nt, 2LL * nsm);
+        for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : ns;
+        auto time_cfg = [&](int kind, int mult, int split, float &ms) -> int {
+            std::vector<int> gr(2 * NQC, std::min(G, mult * nsm)), kd(2 * NQC, kind), sp(2 * NQC, split);
+            int dummy = 0;
+            cudaEventRecord(e0, st);
+            int rc = launch_exec(sub, d_mols, d_tiles + ex.off[k], d_part, d_cnt, nullptr, boys, G, gr.data(),
+                                 false, st, nullptr, dummy, kd.data(), 0, 0, 1, sp.data());
+            cudaEventRecord(e1, st);
+            if (rc != TG_OK) return rc;
+            TG_CUDA(cudaEventSynchronize(e1));
+            ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            return TG_OK;
+        };
+        int bk = 1, bm = 2, bs = 0;
+        float best = -1.f;
+        for (int kind = 1; kind <= 3; ++kind) {
+            float ms;
+            const int rc = time_cfg(kind, bm, bs, ms);
+            if (rc != TG_OK) return rc;
+            if (best < 0.f || ms < best) best = ms, bk = kind;
+        }
+        for (int mult : {1, 4}) {
+            float ms;
+            const int rc = time_cfg(bk, mult, bs, ms);
+            if (rc != TG_OK) return rc;
+            if (ms < best) best = ms, bm = mult;
+        }
+        for (int split : {1, 4}) {
+            float ms;
+            const int rc = time_cfg(bk, bm, split, ms);
+            if (rc != TG_OK) return rc;
+            if (ms < best) best = ms, bs = split;
+        }
+        kinds[k] = bk;
+        grids[k] = std::min(G, bm * nsm);
+        splits[k] = bs;
+    }
+    return TG_OK;
+}
+
 void fill_stats(tg_stats *stats, const unsigned long long *hc, long long pairs, long long tiles, int launches, int G,
                 int nops = 2)
 {
@@ -1282,14 +1355,32 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
     const uint4 *d_tiles = dt.tiles;
     const MolDesc md = make_desc(pl, 0);
     TG_CUDA(cudaMemcpyAsync(d_mol, &md, sizeof(MolDesc), cudaMemcpyHostToDevice, st));
+    // autotune = 1: the per-list launch choices of the basis's first tuned
+    // call; autotune = 2: tune again on this call and keep the new choices
+    int kd[2 * NQC], gr[2 * NQC], sp[2 * NQC];
+    const bool tune = opt.autotune == 1 || opt.autotune == 2;
+    if (tune) {
+        if (!b->tuned || opt.autotune == 2) {
+            rc = tune_lists(ex, d_mol, d_tiles, d_part, pl.dcnt, b->d_boys, pl.G, b->nsm, st, b->tune_kind,
+                            b->tune_grid, b->tune_split);
+            if (rc != TG_OK) return rc;
+            b->tuned = true;
+        }
+        for (int k = 0; k < 2 * NQC; ++k) {
+            kd[k] = b->tune_kind[k] ? b->tune_kind[k] : opt.kernel_kind;
+            gr[k] = b->tune_grid[k];
+            sp[k] = b->tune_split[k];
+        }
+    }
     TG_CUDA(cudaMemsetAsync(d_part, 0, sizeof(double) * (size_t)pl.G * 3 * natom, st));
     TG_CUDA(cudaMemsetAsync(pl.dcnt, 0, sizeof(unsigned long long) * NCNT * NQC, st));
     if (stats)
         for (int qc = 0; qc < NQC; ++qc) stats->class_ms[qc] = stats->class_ms_fp32[qc] = 0.0;
     const double plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     // (a tile shard is already in the lists)
-    rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, nullptr, b->d_boys, pl.G, nullptr, opt.timing != 0, st,
-                     stats, launches, nullptr, opt.kernel_kind);
+    rc = launch_exec(ex, d_mol, d_tiles, d_part, pl.dcnt, nullptr, b->d_boys, pl.G, tune ? gr : nullptr,
+                     opt.timing != 0, st, stats, launches, tune ? kd : nullptr, opt.kernel_kind, 0, 1,
+                     tune ? sp : nullptr);
     if (rc != TG_OK) return rc;
     k_reduce<<<(3 * natom + 127) / 128, 128, 0, st>>>(3 * natom, pl.G, d_part, pl.dgrad);
     ++launches;
@@ -1617,68 +1708,21 @@ int tg_batch_create(int nmol, const tg_basis *const *bases, const int *npair, co
                            cudaMemcpyHostToDevice));
     const double *boys = bt->bases[0]->d_boys;
 
-    // ---- autotune every (class, precision) list on a sample of its first
-    // tiles (the costliest: the lists are sorted by decreasing cost): kernel
-    // form (thread, group, warp), grid capped at 1, 2 or 4 CTAs per SM, and
-    // unit shape (bra-primitive splits per tile: automatic, 1 or 4), searched
-    // one coordinate at a time from (default form, 2 CTAs per SM, automatic
-    // splits): the fastest form, then the fastest grid cap for it, then the
-    // fastest split -- 7 timed launches per list instead of the 27 of the
-    // full product
+    // ---- autotune every (class, precision) list (tune_lists)
     bt->grids.assign(2 * NQC, G);
     bt->kinds.assign(2 * NQC, opt.kernel_kind);
     bt->splits.assign(2 * NQC, 0);
     const int nsm = std::max(1, bt->bases[0]->nsm);
-    if (opt.autotune == 1) {
-        EventPair ev;
-        TG_CUDA(ev.create());
-        cudaEvent_t e0 = ev.a, e1 = ev.b;
+    if (opt.autotune == 1 || opt.autotune == 2) {
+        int kd[2 * NQC], gr[2 * NQC], sp[2 * NQC];
+        const int rc = tune_lists(bt->ex, bt->d_mols, bt->d_tiles, bt->d_part, bt->d_cnt, boys, G, nsm, st, kd, gr,
+                                  sp);
+        if (rc != TG_OK) return rc;
         for (int k = 0; k < 2 * NQC; ++k) {
-            const long long nt = bt->ex.off[k + 1] - bt->ex.off[k];
-            if (nt <= nsm) continue;
-            Exec sub;
-            sub.natom_total = natom_total;
-            sub.natom_max = natom_max;
-            const long long ns = std::min<long long>(nt, 2LL * nsm);
-            for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : ns;
-            auto time_cfg = [&](int kind, int mult, int split, float &ms) -> int {
-                std::vector<int> gr(2 * NQC, mult * nsm), kd(2 * NQC, kind), sp(2 * NQC, split);
-                int dummy = 0;
-                cudaEventRecord(e0, st);
-                int rc = launch_exec(sub, bt->d_mols, bt->d_tiles + bt->ex.off[k], bt->d_part, bt->d_cnt, nullptr,
-                                     boys, G, gr.data(), false, st, nullptr, dummy, kd.data(), 0, 0, 1, sp.data());
-                cudaEventRecord(e1, st);
-                if (rc != TG_OK) return rc;
-                TG_CUDA(cudaEventSynchronize(e1));
-                ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                return TG_OK;
-            };
-            int bk = 0, bm = 2, bs = 0;
-            float best = -1.f;
-            for (int kind = 1; kind <= 3; ++kind) {
-                float ms;
-                const int rc = time_cfg(kind, bm, bs, ms);
-                if (rc != TG_OK) return rc;
-                if (best < 0.f || ms < best) best = ms, bk = kind;
-            }
-            for (int mult : {1, 4}) {
-                float ms;
-                const int rc = time_cfg(bk, mult, bs, ms);
-                if (rc != TG_OK) return rc;
-                if (ms < best) best = ms, bm = mult;
-            }
-            for (int split : {1, 4}) {
-                float ms;
-                const int rc = time_cfg(bk, bm, split, ms);
-                if (rc != TG_OK) return rc;
-                if (ms < best) best = ms, bs = split;
-            }
-            bt->grids[k] = bm * nsm;
-            bt->kinds[k] = bk;
-            bt->splits[k] = bs;
+            if (kd[k]) bt->kinds[k] = kd[k];
+            if (gr[k]) bt->grids[k] = gr[k];
+            bt->splits[k] = sp[k];
         }
-        bt->G = G = std::max(G, *std::max_element(bt->grids.begin(), bt->grids.end()));
     }
     // the partial slabs must cover the largest tuned grid
     if ((size_t)G * 3 * natom_total > (size_t)bt->plans[0].G * 3 * natom_total) {
