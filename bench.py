@@ -460,8 +460,9 @@ def main():
     ap.add_argument("--bound-steps", type=int, default=1, help="timed mixed-bound steps for the comparison (0: skip)")
     ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
     ap.add_argument("--fock", action="store_true", help="time the Fock-type build (tg_fock2e) instead")
-    ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
-                    help="1: tg_options.autotune = 1 (launches tuned per class list on the first warm-up call)")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="1 (default): tg_options.autotune = 1, launches tuned per class list on the first "
+                         "warm-up call and reused; 0: the per-class default forms")
     ap.add_argument("--shard", type=int, default=1, help="c4, c5: time tile-cyclic shard 0 of this many")
     args = ap.parse_args()
     if args.opcount:

@@ -307,19 +307,23 @@ def test_allocation_failure_leaves_the_output_untouched(tg, monkeypatch):
 
 def test_autotuned_single_calls(tg):
     """tg_grad2e with autotune = 1 tunes the launches of every class list on the
-    basis's first such call and reuses them: the fp64 gradient stays within the
-    plain bound of the oracle, a second tuned call repeats the first bitwise, and
-    a re-tune (autotune = 2) changes nothing beyond rounding."""
-    s = synth.molecule(18, 4, 4)
-    ref, _, nq = oracle.grad2e(s, tau=1e-10)
+    basis's first such call and reuses them.  On full-size c2 (lists of more
+    than 152 tiles, so the tuner runs): a pair-key shard stays within the plain
+    bound of the oracle's shard, a second tuned call repeats the first bitwise,
+    a re-tune (autotune = 2) stays within the bound, and the whole tuned
+    gradient equals the untuned one up to summation order."""
+    s = synth.config(1)
+    ref, _, nq = oracle.grad2e(s, tau=1e-10, rank=7, nranks=3000)
     b = tg.Basis(s)
-    g1, st1 = b.grad2e(s["pairs"], screen_tol=1e-10, autotune=1)
-    assert st1["quartets"] == nq
+    kw = dict(screen_tol=1e-10, rank=7, nranks=3000)
+    g1, st1 = b.grad2e(s["pairs"], autotune=1, **kw)
+    assert st1["quartets"] == nq and nq > 0
     assert np.abs(g1 - ref).max() <= TOL
-    g2, _ = b.grad2e(s["pairs"], screen_tol=1e-10, autotune=1)
+    g2, _ = b.grad2e(s["pairs"], autotune=1, **kw)
     assert np.array_equal(g1, g2)
-    g3, _ = b.grad2e(s["pairs"], screen_tol=1e-10, autotune=2)
+    g3, _ = b.grad2e(s["pairs"], autotune=2, **kw)
     assert np.abs(g3 - ref).max() <= TOL
-    gm, stm = b.grad2e(s["pairs"], screen_tol=1e-10, precision=tg.TG_MIXED_BOUND, mixed_tol=1e-6, autotune=1)
-    assert np.abs(gm - ref).max() <= 1e-6
-    assert 0 < stm["fp32_quartets"] < stm["quartets"]
+    whole, stw = b.grad2e(s["pairs"], screen_tol=1e-10)
+    tuned, stt = b.grad2e(s["pairs"], screen_tol=1e-10, autotune=1)
+    assert stt["quartets"] == stw["quartets"]
+    assert np.abs(tuned - whole).max() <= 1e-11
