@@ -152,7 +152,8 @@ typedef struct {
     long long prim_quartets;      /* primitive quartets evaluated */
     long long fp32_quartets;      /* quartets routed to fp32 */
     long long pairs;              /* shell pairs kept after pair screening */
-    long long tiles;              /* quartet tiles launched */
+    long long tiles;              /* quartet tiles of the call after screening (tg_grad2e:
+                                     the whole system's, before a TG_SHARD_TILES shard) */
     int launches;                 /* CUDA kernels launched by the call */
     int grid;                     /* CTAs of each persistent class launch */
     double class_ms[21];          /* per angular class: fp64 kernel time (only with timing = 1) */
