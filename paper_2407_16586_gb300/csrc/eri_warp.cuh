@@ -120,6 +120,24 @@ __device__ __forceinline__ float boys_order_fp32(float T, int m, const double *_
     return f;
 }
 
+// Shared memory of a warp-kernel CTA (TILE / 32 warps of base_n + q * per_q
+// elements of fsize bytes, the item lists, and the tile staging plus the
+// per-CTA gradient slab of a molecule of up to 32 atoms) and the largest
+// q <= q0 (at least 4) with which two such CTAs fit in one SM's 228 KB
+// (1 KB reserved per CTA); 0 if none does.
+constexpr size_t warp_cta_bytes(size_t fsize, int base_n, int per_q, size_t list_bytes, int q)
+{
+    return (size_t)(TILE / 32) * ((fsize * (size_t)(base_n + q * per_q) + 15) & ~(size_t)15) + list_bytes + 64 +
+           (size_t)TILE * 12 * sizeof(double) + (size_t)TILE * 4 * sizeof(int) + 6 * (TB + TK) * sizeof(double) +
+           2 * (TB + TK) * sizeof(int) + 3 * 32 * sizeof(double);
+}
+constexpr int warp_qt_two_ctas(size_t fsize, int base_n, int per_q, size_t list_bytes, int q0)
+{
+    for (int q = q0; q >= 4; --q)
+        if (2 * (warp_cta_bytes(fsize, base_n, per_q, list_bytes, q) + 1024) <= 228 * 1024) return q;
+    return 0;
+}
+
 template <int LA, int LB, int LC, int LD, typename F>
 struct WarpLayout {
     static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
@@ -137,9 +155,18 @@ struct WarpLayout {
     // then, per operator, the base multipliers pref_op * mul_op^m for m <= L + 1
     static constexpr int SC_PW = SC_POW + L + 3;
     static constexpr int NSC = SC_PW + 2 * (L + 2);
-    // ket primitive pairs whose 1-D tables and scalars are kept at a time
-    static constexpr int QT_RAW = (int)((6144 / sizeof(F)) / (3 * EKN + NSC));
-    static constexpr int QT = QT_RAW < 4 ? 4 : (QT_RAW > 32 ? 32 : QT_RAW);
+    // ket primitive pairs whose 1-D tables and scalars are kept at a time: a
+    // 6 KB budget per warp, lowered (not below 4) where that lets two CTAs
+    // share an SM on small molecules
+    static constexpr int PER_Q = 3 * EKN + NSC;
+    static constexpr int BASE_N = 2 * NAB * NCD + 2 * NCD * NH1 + 2 * NCD * NH1P + NAB * NH1 + NCD * NH2 + 2 * NR +
+                                  2 * (L + 2) + 3 * EBN;
+    static constexpr int QT_RAW = (int)((6144 / sizeof(F)) / PER_Q);
+    static constexpr int QT0 = QT_RAW < 4 ? 4 : (QT_RAW > 32 ? 32 : QT_RAW);
+    static constexpr int ZMAX = NCD * NH2P, YMAX = NAB * NH1P;
+    static constexpr size_t LIST_BYTES = (sizeof(unsigned) * (size_t)(ZMAX + YMAX) + 15) & ~(size_t)15;
+    static constexpr int QT_FIT = warp_qt_two_ctas(sizeof(F), BASE_N, PER_Q, LIST_BYTES, QT0);
+    static constexpr int QT = QT_FIT > 0 ? QT_FIT : QT0;
     // element offsets (F units)
     static constexpr int o_gam = 0;                          // [2][NAB][NCD]
     static constexpr int o_F = o_gam + 2 * NAB * NCD;        // [2][NCD][NH1]
@@ -153,10 +180,9 @@ struct WarpLayout {
     static constexpr int o_sc = o_Ek + QT * 3 * EKN;         // [QT][NSC]
     static constexpr int TOTAL = o_sc + QT * NSC;
     static constexpr size_t BYTES = (sizeof(F) * (size_t)TOTAL + 15) & ~(size_t)15;
-    // CTA-wide lists of the (cd, h2) items of z and the (ab, h1) items of Y that
-    // lie in a derivative box (built once per CTA)
-    static constexpr int ZMAX = NCD * NH2P, YMAX = NAB * NH1P;
-    static constexpr size_t LIST_BYTES = (sizeof(unsigned) * (size_t)(ZMAX + YMAX) + 15) & ~(size_t)15;
+    static_assert(o_Ek == BASE_N, "BASE_N counts every array ahead of the ket tables");
+    // (ZMAX, YMAX, LIST_BYTES above: the CTA-wide lists of the (cd, h2) items of
+    // z and the (ab, h1) items of Y that lie in a derivative box, built once per CTA)
     // W items per lane (kept in registers over the ket primitives)
     static constexpr int KW = (NCD * NH1P + 31) / 32;
     __host__ __device__ static constexpr size_t bytes() { return BYTES; }
