@@ -184,6 +184,13 @@ def test_error_codes(tg, c1):
     with pytest.raises(tg.TGError) as e:
         basis.grad2e([(a, a, 1, 0, 0, 0)], rank=2, nranks=2)
     assert e.value.status == tg.TG_EINVAL
+    # named options out of range
+    for kw in (dict(kernel=4), dict(shard_mode=2), dict(class_mask=1 << 21), dict(autotune=3)):
+        out = np.full((c1["natom"], 3), 5.0)
+        with pytest.raises(tg.TGError) as e:
+            basis.grad2e([(a, a, 1, 0, 0, 0)], out=out, **kw)
+        assert e.value.status == tg.TG_EINVAL, kw
+        assert np.all(out == 5.0)
 
 
 def test_fp32_route_close_to_fp64(tg, c1):
