@@ -245,7 +245,8 @@ int tg_fock2e(const tg_basis *b, int npair, const tg_fpair *pairs, const tg_opti
  * device_ptrs the densities are read from the caller's device buffers at
  * every run (their contents may change, the plan does not), otherwise they
  * are copied at creation.  opt->autotune = 1 autotunes every class list
- * on its costliest 2 x (SM count) tiles: the kernel form (thread, group or
+ * on a sample of 2 to 4 x (SM count) of its tiles taken at a fixed stride
+ * over the whole list: the kernel form (thread, group or
  * warp), the persistent grid (1, 2 or 4 CTAs per SM) and the work-unit shape
  * (bra primitive splits per tile: automatic, 1 or 4), searched one
  * coordinate at a time (form, then grid, then splits; 7 timed launches per

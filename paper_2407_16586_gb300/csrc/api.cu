@@ -1192,8 +1192,9 @@ void alu_peaks(double &p64, double &p32)
 }
 
 // Autotuner of the class launches: for every (class, precision) list of ex
-// with more than nsm tiles, time its costliest 2 x nsm tiles (the lists are
-// sorted by decreasing cost) and search the kernel form (thread, group,
+// with more than nsm tiles, time a sample of 2 to 4 x nsm tiles taken at a
+// fixed stride over the whole list (whose tiles run from the costliest to
+// the cheapest) and search the kernel form (thread, group,
 // warp), the grid cap (1, 2 or 4 CTAs per SM) and the unit shape (bra
 // primitive splits per tile: automatic, 1 or 4) one coordinate at a time
 // from (form 1, 2 CTAs per SM, automatic splits): the
@@ -1216,14 +1217,16 @@ int tune_lists(const Exec &ex, const MolDesc *d_mols, const uint4 *d_tiles, doub
         Exec sub;
         sub.natom_total = ex.natom_total;
         sub.natom_max = ex.natom_max;
-        const long long ns = std::min<long long>(nt, 2LL * nsm);
-        for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : ns;
+        // the sample: every step-th tile of the list (2 to 4 x nsm tiles spread
+        // over its whole cost range, through the tile-shard stride)
+        const int step = (int)std::max<long long>(1, nt / (2LL * nsm));
+        for (int j = 0; j < 2 * NQC + 1; ++j) sub.off[j] = j <= k ? 0 : nt;
         auto time_cfg = [&](int kind, int mult, int split, float &ms) -> int {
             std::vector<int> gr(2 * NQC, std::min(G, mult * nsm)), kd(2 * NQC, kind), sp(2 * NQC, split);
             int dummy = 0;
             cudaEventRecord(e0, st);
             int rc = launch_exec(sub, d_mols, d_tiles + ex.off[k], d_part, d_cnt, nullptr, boys, G, gr.data(),
-                                 false, st, nullptr, dummy, kd.data(), 0, 0, 1, sp.data());
+                                 false, st, nullptr, dummy, kd.data(), 0, 0, step, sp.data());
             cudaEventRecord(e1, st);
             if (rc != TG_OK) return rc;
             TG_CUDA(cudaEventSynchronize(e1));
