@@ -407,6 +407,74 @@ def run_large(args, prec, router, torch):
     return 0
 
 
+def run_spherical(args, prec, router, torch):
+    """Spherical shells (tg_grad2e_sph) on the same molecule: densities over
+    the 2l+1 spherical functions per shell (drawn with the c2 recipe at the
+    spherical size), transformed to the Cartesian basis on the device inside
+    every step.  Device-resident densities timed with CUDA events; e2e with
+    host densities in pinned memory and the gradient read back."""
+    import numpy as np
+    import paper_2407_16586_gb300 as tg
+    s, wname = workload(args.workload)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    basis = tg.Basis(s)
+    n = basis.nsph
+    rng = np.random.default_rng(16586)
+    mats = []
+    for _ in range(2):
+        c = rng.normal(0.0, 0.3, size=(n, 5))
+        mats.append(c @ c.T)
+    x = rng.normal(size=(n, n))
+    mats.append(x / np.linalg.norm(x))
+    P, Pd, X = mats
+    hp = [(P, P, 1.0, 0.157706, 1.0, 0.3), (Pd, P, 1.0, 0.157706, 1.0, 0.3), (X, X, 1.0, 0.157706, 1.0, 0.3)]
+    dp = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev), cj, ck, cl, om) for (a, b, cj, ck, cl, om) in hp]
+    gout = torch.empty((s["natom"], 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    kw = dict(screen_tol=TAU, precision=prec, router=router, spherical=True, autotune=args.autotune)
+    for _ in range(args.warmup):
+        _, st0 = basis.grad2e(dp, out=gout, **kw)
+    ms, q = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = basis.grad2e(dp, out=gout, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += e0.elapsed_time(e1)
+        q += st["quartets"]
+    pint = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory(), cj, ck, cl, om)
+            for (a, b, cj, ck, cl, om) in hp]
+    pin = [(a.numpy(), b.numpy(), cj, ck, cl, om) for (a, b, cj, ck, cl, om) in pint]
+    hout_t = torch.zeros((s["natom"], 3), dtype=torch.float64).pin_memory()
+    hout = hout_t.numpy()
+    e2e_ms, e2e_q = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        _, st = basis.grad2e(pin, out=hout, stream=stream.cuda_stream, **kw)
+        e2e_ms += 1e3 * (time.perf_counter() - t)
+        e2e_q += st["quartets"]
+    line = {"metric": METRIC + ", spherical shells", "value": q / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec != tg.TG_FP64 else "f64",
+            "data": "synthetic",
+            "config": {"workload": wname + "; densities over %d spherical functions (%d Cartesian)" % (n, basis.nbf),
+                       "precision": args.precision, "screen_tol": TAU, "quartets_per_step": st0["quartets"],
+                       "fp32_quartets_per_step": st0["fp32_quartets"],
+                       "l2": "flushed (512 MB write) before each timed step"},
+            "e2e": {"value": e2e_q / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": sum(a.nbytes + b.nbytes for (a, b, *_r) in pin),
+                    "d2h_bytes_per_step": hout.nbytes},
+            "gpu_launches": st0["launches"]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_fock(args, torch):
     """The Fock-type build on the same workload (Sec. II.B, eq. G_2e: the
     relaxed difference density with c_J = 2, c_K = -alpha, c_K_lr = -beta;
@@ -460,6 +528,7 @@ def main():
     ap.add_argument("--bound-steps", type=int, default=1, help="timed mixed-bound steps for the comparison (0: skip)")
     ap.add_argument("--opcount", action="store_true", help="print the FLOP model per angular class and exit")
     ap.add_argument("--fock", action="store_true", help="time the Fock-type build (tg_fock2e) instead")
+    ap.add_argument("--spherical", action="store_true", help="time tg_grad2e_sph (spherical shells) instead")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1 (default): tg_options.autotune = 1, launches tuned per class list on the first "
                          "warm-up call and reused; 0: the per-class default forms")
@@ -499,6 +568,8 @@ def main():
 
     if args.fock:
         return run_fock(args, torch)
+    if args.spherical:
+        return run_spherical(args, prec, router, torch)
     if args.workload.startswith("c3"):
         return run_c3(args, prec, router, torch)
     if args.workload in ("c4", "c5"):

@@ -208,6 +208,22 @@ void tg_basis_destroy(tg_basis *b);
 int tg_grad2e(const tg_basis *b, int npair, const tg_pair *pairs, const tg_options *opt,
               double *grad, tg_stats *stats);
 
+/* Spherical shells (Sec. II.C: a shell's 2l+1 spherical functions are a
+ * spherical transformation of its Cartesian ones).  The same gradient as
+ * tg_grad2e, of the integrals over spherical functions: every A and B of
+ * pairs is tg_basis_nsph(b) x tg_basis_nsph(b), row-major, in the spherical
+ * AO order -- per shell in shell order: s; p as x, y, z; d as the unit-norm
+ * real solid harmonics m = -2 (sqrt3 xy), -1 (sqrt3 yz), 0 (zz - (xx+yy)/2),
+ * +1 (sqrt3 xz), +2 ((sqrt3/2)(xx - yy)) of the x^l-normalised Cartesian
+ * functions.  The library forms A_cart = T A T^T (T: nbf x nsph, block
+ * diagonal over shells) on the device and runs tg_grad2e on them, which
+ * gives sum d(mn|ls)_sph A B exactly (linearity).  Options, stats and
+ * errors as tg_grad2e (host pointers unless device_ptrs); stats.launches
+ * also counts the 2 * npair transforms. */
+int tg_basis_nsph(const tg_basis *b);
+int tg_grad2e_sph(const tg_basis *b, int npair, const tg_pair *pairs, const tg_options *opt,
+                  double *grad, tg_stats *stats);
+
 const char *tg_strerror(int status);
 
 /* ---- Fock-type build (Sec. II.B: the two-electron part of eq. G_2e, the

@@ -106,6 +106,43 @@ def _nc(l):
     return (l + 1) * (l + 2) // 2
 
 
+def sph_transform(s):
+    """Cartesian-to-spherical matrix T (ncart x nsph) of the basis, block
+    diagonal over shells (Sec. II.C: the 2l+1 spherical functions of a shell
+    follow from its Cartesian ones by a spherical transformation).  Column m
+    of a shell's block holds the coefficients of spherical function m in its
+    Cartesian components (x^l normalised, order xx xy xz yy yz zz for d):
+      s: 1;  p: x, y, z;
+      d: m = -2: sqrt3 xy, -1: sqrt3 yz, 0: zz - (xx + yy) / 2,
+         +1: sqrt3 xz, +2: sqrt3 / 2 (xx - yy),
+    the real solid harmonics r^2 Y_2m written in Cartesian monomials and
+    scaled to unit norm.  A spherical-basis density A enters the Cartesian
+    integrals as T A T^T."""
+    ls = [int(l) for l in s["shell_l"]]
+    nc = sum(_nc(l) for l in ls)
+    ns = sum(2 * l + 1 for l in ls)
+    T = np.zeros((nc, ns))
+    r3 = np.sqrt(3.0)
+    d = np.zeros((6, 5))
+    # columns m = -2, -1, 0, +1, +2; rows xx, xy, xz, yy, yz, zz
+    d[1, 0] = r3
+    d[4, 1] = r3
+    d[5, 2], d[0, 2], d[3, 2] = 1.0, -0.5, -0.5
+    d[2, 3] = r3
+    d[0, 4], d[3, 4] = r3 / 2.0, -r3 / 2.0
+    i = j = 0
+    for l in ls:
+        if l < 2:
+            T[i:i + _nc(l), j:j + 2 * l + 1] = np.eye(_nc(l))
+        elif l == 2:
+            T[i:i + 6, j:j + 5] = d
+        else:
+            raise ValueError("l > 2")
+        i += _nc(l)
+        j += 2 * l + 1
+    return T
+
+
 def shell_eri(s, a, b, c, d, omega=0.0):
     """Contracted (ab|cd) for one shell quartet; omega>0 selects erf(omega r)/r."""
     bs = _Basis(s)

@@ -34,8 +34,8 @@ TG_MAX_PAIRS = 8
 TG_SHARD_PAIR_KEY = 0
 TG_SHARD_TILES = 1
 
-EXPORTS = ("tg_options_default", "tg_abi_version", "tg_class_flops", "tg_tile_shard", "tg_fock2e", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_destroy",
-           "tg_grad2e", "tg_strerror", "tg_tile_samples", "tg_router_nparam", "tg_router_create",
+EXPORTS = ("tg_options_default", "tg_abi_version", "tg_class_flops", "tg_tile_shard", "tg_fock2e", "tg_basis_create", "tg_basis_nbf", "tg_basis_natom", "tg_basis_nsph", "tg_basis_destroy",
+           "tg_grad2e", "tg_grad2e_sph", "tg_strerror", "tg_tile_samples", "tg_router_nparam", "tg_router_create",
            "tg_router_destroy", "tg_router_get", "tg_router_set", "tg_router_train", "tg_router_loss_grad",
            "tg_router_predict", "tg_router_save", "tg_router_load", "tg_batch_create", "tg_batch_run",
            "tg_batch_destroy")
@@ -110,6 +110,10 @@ def lib():
         L.tg_grad2e.argtypes = [vp, ctypes.c_int, ctypes.POINTER(tg_pair), ctypes.POINTER(tg_options), vp,
                                 ctypes.POINTER(tg_stats)]
         L.tg_grad2e.restype = ctypes.c_int
+        L.tg_grad2e_sph.argtypes = L.tg_grad2e.argtypes
+        L.tg_grad2e_sph.restype = ctypes.c_int
+        L.tg_basis_nsph.argtypes = [vp]
+        L.tg_basis_nsph.restype = ctypes.c_int
         L.tg_strerror.argtypes = [ctypes.c_int]
         L.tg_strerror.restype = ctypes.c_char_p
         fp = ctypes.POINTER(ctypes.c_float)
@@ -203,20 +207,26 @@ def tg_basis_natom(h):
     return lib().tg_basis_natom(h)
 
 
+def tg_basis_nsph(h):
+    return lib().tg_basis_nsph(h)
+
+
 def tg_basis_destroy(h):
     lib().tg_basis_destroy(h)
 
 
-def tg_grad2e(h, pairs, options=None, grad_ptr=None, natom=None):
+def tg_grad2e(h, pairs, options=None, grad_ptr=None, natom=None, spherical=False):
     """pairs: list of (A_ptr, B_ptr, c_J, c_K, c_K_lr, omega) with raw pointers
     (host or device per options.device_ptrs).  grad_ptr: raw output pointer;
-    returns (status, tg_stats)."""
+    spherical: the matrices are over spherical functions (tg_grad2e_sph).
+    Returns (status, tg_stats)."""
     arr = (tg_pair * len(pairs))()
     for i, (a, b, cj, ck, cl, om) in enumerate(pairs):
         arr[i] = tg_pair(a, b, cj, ck, cl, om)
     st = tg_stats()
     opt = options if options is not None else tg_options_default()
-    rc = lib().tg_grad2e(h, len(pairs), arr, ctypes.byref(opt), grad_ptr, ctypes.byref(st))
+    fn = lib().tg_grad2e_sph if spherical else lib().tg_grad2e
+    rc = fn(h, len(pairs), arr, ctypes.byref(opt), grad_ptr, ctypes.byref(st))
     return rc, st
 
 
@@ -229,6 +239,7 @@ class Basis:
         self.h = tg_basis_create(self.natom, system["xyz"], self.nshell, system["shell_atom"], system["shell_l"],
                                  system["shell_nprim"], system["exps"], system["coefs"])
         self.nbf = tg_basis_nbf(self.h)
+        self.nsph = tg_basis_nsph(self.h)
 
     def close(self):
         if self.h is not None:
@@ -291,14 +302,16 @@ class Basis:
         return F, st.as_dict()
 
     def grad2e(self, pairs, screen_tol=1e-10, precision=TG_FP64, rank=0, nranks=1, stream=None, out=None,
-               timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0, shard_mode=0, autotune=0):
+               timing=False, router=None, mixed_tol=1e-6, kernel=0, class_mask=0, shard_mode=0, autotune=0,
+               spherical=False):
         """Gradient (natom x 3) of host numpy pairs [(A, B, c_J, c_K, c_K_lr, omega)], or of
         torch CUDA tensors (then the densities and ``out`` stay on the device).  ``kernel``
         picks the class kernels: 0 per-class default, 1 one quartet per thread, 2 a thread
         group per quartet where compiled, 3 a warp per quartet where compiled.  ``class_mask``
         (0 = all) keeps the angular classes whose bits are set.  ``autotune`` 1 tunes the
         launches of every class list on this basis's first such call and reuses them, 2
-        tunes again (tg_options.autotune)."""
+        tunes again (tg_options.autotune).  ``spherical``: the matrices are nsph x nsph over
+        spherical functions (tg_grad2e_sph)."""
         opt = tg_options_default()
         opt.kernel_kind = int(kernel)
         opt.autotune = int(autotune)
@@ -328,14 +341,14 @@ class Basis:
             opt.device_ptrs = 1
             opt.stream = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
             g = out if out is not None else torch.empty((self.natom, 3), dtype=torch.float64, device=pairs[0][0].device)
-            rc, st = tg_grad2e(self.h, plist, opt, ctypes.c_void_p(g.data_ptr()))
+            rc, st = tg_grad2e(self.h, plist, opt, ctypes.c_void_p(g.data_ptr()), spherical=spherical)
         else:
             g = out if out is not None else np.zeros((self.natom, 3))
             if stream is not None:
                 opt.stream = ctypes.c_void_p(stream)
-            rc, st = tg_grad2e(self.h, plist, opt, ctypes.c_void_p(g.ctypes.data))
+            rc, st = tg_grad2e(self.h, plist, opt, ctypes.c_void_p(g.ctypes.data), spherical=spherical)
         if rc != TG_OK:
-            raise TGError(rc, "tg_grad2e")
+            raise TGError(rc, "tg_grad2e_sph" if spherical else "tg_grad2e")
         return g, st.as_dict()
 
 

@@ -93,6 +93,11 @@ struct tg_basis {
     // first such call and kept for the later ones
     bool tuned = false;
     int tune_kind[2 * NQC], tune_grid[2 * NQC], tune_split[2 * NQC];
+    // spherical shells: 2l+1 functions per shell; per Cartesian function its
+    // shell's first spherical function << 8 | l << 4 | Cartesian component
+    int nsph = 0;
+    std::vector<int> cmap;
+    DevArena ws6;  // tg_grad2e_sph: spherical and Cartesian densities, gradient
 };
 
 namespace {
@@ -133,6 +138,7 @@ void free_basis(tg_basis *b)
     b->ws3.release();
     b->ws4.release();
     b->ws5.release();
+    b->ws6.release();
 }
 
 int basis_setup(tg_basis *b, const double *xyz, const double *exps, const double *coefs)
@@ -299,13 +305,17 @@ int tg_basis_create(int natom, const double *xyz, int nshell, const int *shell_a
     b->sh_nprim.assign(shell_nprim, shell_nprim + nshell);
     b->sh_poff.resize(nshell);
     b->sh_bf.resize(nshell);
-    int po = 0, bo = 0;
+    int po = 0, bo = 0, so = 0;
+    b->cmap.resize(nbf);
     for (int s = 0; s < nshell; ++s) {
         b->sh_poff[s] = po;
         b->sh_bf[s] = bo;
+        for (int c = 0; c < ncart(shell_l[s]); ++c) b->cmap[bo + c] = (so << 8) | (shell_l[s] << 4) | c;
         po += shell_nprim[s];
         bo += ncart(shell_l[s]);
+        so += 2 * shell_l[s] + 1;
     }
+    b->nsph = so;
     int rc = basis_setup(b, xyz, exps, coefs);
     if (rc != TG_OK) {
         free_basis(b);
@@ -318,6 +328,7 @@ int tg_basis_create(int natom, const double *xyz, int nshell, const int *shell_a
 
 int tg_basis_nbf(const tg_basis *b) { return b ? b->nbf : TG_EINVAL; }
 int tg_basis_natom(const tg_basis *b) { return b ? b->natom : TG_EINVAL; }
+int tg_basis_nsph(const tg_basis *b) { return b ? b->nsph : TG_EINVAL; }
 
 void tg_basis_destroy(tg_basis *b)
 {
@@ -1398,6 +1409,60 @@ int tg_grad2e(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_opti
         stats->plan_ms = plan_ms;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    return TG_OK;
+}
+
+int tg_grad2e_sph(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_options *opt_in, double *grad,
+                  tg_stats *stats)
+{
+    tg_basis *b = const_cast<tg_basis *>(cb);
+    if (!b || !pairs || !grad) return TG_EINVAL;
+    tg_options opt;
+    if (opt_in) opt = *opt_in;
+    else tg_options_default(&opt);
+    if (npair < 1) return TG_EINVAL;
+    if (npair > TG_MAX_PAIRS) return TG_EUNSUPPORTED;
+    for (int p = 0; p < npair; ++p)
+        if (!pairs[p].A || !pairs[p].B) return TG_EINVAL;
+    cudaStream_t st = (cudaStream_t)opt.stream;
+    const size_t nbf = (size_t)b->nbf, nsph = (size_t)b->nsph, natom = (size_t)b->natom;
+    const int nup = opt.device_ptrs ? 0 : 2 * npair;
+    const size_t need = al(sizeof(double) * nsph * nsph) * nup + al(sizeof(double) * nbf * nbf) * 2 * npair +
+                        al(sizeof(int) * nbf) + al(sizeof(double) * 3 * natom) + 4096;
+    DevArena &W = b->ws6;
+    TG_CUDA(W.reserve(need));
+    W.used = 0;
+    int *d_cmap = W.take<int>(nbf);
+    double *d_grad = W.take<double>(3 * natom);
+    TG_CUDA(cudaMemcpyAsync(d_cmap, b->cmap.data(), sizeof(int) * nbf, cudaMemcpyHostToDevice, st));
+    tg_pair cp[TG_MAX_PAIRS];
+    const unsigned gs = (unsigned)((nbf * nbf + 255) / 256);
+    for (int p = 0; p < npair; ++p) {
+        const double *src[2] = {pairs[p].A, pairs[p].B};
+        double *dst[2];
+        for (int k = 0; k < 2; ++k) {
+            const double *a = src[k];
+            if (!opt.device_ptrs) {
+                double *up = W.take<double>(nsph * nsph);
+                TG_CUDA(cudaMemcpyAsync(up, a, sizeof(double) * nsph * nsph, cudaMemcpyHostToDevice, st));
+                a = up;
+            }
+            dst[k] = W.take<double>(nbf * nbf);
+            k_sph_to_cart<<<gs, 256, 0, st>>>((int)nbf, (int)nsph, d_cmap, a, dst[k]);
+            TG_CUDA(cudaGetLastError());
+        }
+        cp[p] = pairs[p];
+        cp[p].A = dst[0];
+        cp[p].B = dst[1];
+    }
+    tg_options o2 = opt;
+    o2.device_ptrs = 1;
+    int rc = tg_grad2e(cb, npair, cp, &o2, d_grad, stats);
+    if (rc != TG_OK) return rc;
+    TG_CUDA(cudaMemcpyAsync(grad, d_grad, sizeof(double) * 3 * natom,
+                            opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    TG_CUDA(cudaStreamSynchronize(st));
+    if (stats) stats->launches += 2 * npair;
     return TG_OK;
 }
 

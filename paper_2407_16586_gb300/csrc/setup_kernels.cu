@@ -360,4 +360,53 @@ __global__ void k_reduce(int n, int nslab, const double *partials, double *grad)
     grad[k] = s;
 }
 
+// Spherical shells (Sec. II.C: the 2l+1 spherical functions of a shell are a
+// fixed combination of its Cartesian ones).  With the Cartesian components
+// normalised as x^l (every component of a shell carries the same N_k N_c),
+// the real solid harmonics of a d shell, each of unit norm, are
+//   m = -2: sqrt3 xy   m = -1: sqrt3 yz   m = 0: zz - (xx + yy)/2
+//   m = +1: sqrt3 xz   m = +2: (sqrt3/2) (xx - yy),
+// so phi_m = sum_c T[c][m] chi_c with the table below (Cartesian order xx,
+// xy, xz, yy, yz, zz); s and p shells keep their functions (p: x, y, z).
+// A density over spherical functions enters the Cartesian integrals as
+// A_cart = T A_sph T^T (T block diagonal over shells), since
+// sum (mn|ls)_sph A_mn B_ls = sum (mn|ls)_cart (T A T^T)_mn (T B T^T)_ls.
+__device__ const double kSphD[6][5] = {
+    {0.0, 0.0, -0.5, 0.0, 0.86602540378443865},   // xx
+    {1.7320508075688772, 0.0, 0.0, 0.0, 0.0},      // xy
+    {0.0, 0.0, 0.0, 1.7320508075688772, 0.0},      // xz
+    {0.0, 0.0, -0.5, 0.0, -0.86602540378443865},  // yy
+    {0.0, 1.7320508075688772, 0.0, 0.0, 0.0},      // yz
+    {0.0, 0.0, 1.0, 0.0, 0.0}};                    // zz
+
+__device__ __forceinline__ double sph_coef(int l, int c, int m)
+{
+    return l == 2 ? kSphD[c][m] : (c == m ? 1.0 : 0.0);
+}
+
+// One element of A_cart per thread.  cmap[i] for Cartesian function i packs
+// the first spherical function of its shell (bits 8..), l (bits 4..7) and its
+// Cartesian component (bits 0..3).
+__global__ void k_sph_to_cart(int nbf, int nsph, const int *__restrict__ cmap, const double *__restrict__ Asph,
+                              double *Acart)
+{
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)nbf * nbf) return;
+    const int i = (int)(id / nbf), j = (int)(id % nbf);
+    const int ci = cmap[i], cj = cmap[j];
+    const int si = ci >> 8, li = (ci >> 4) & 15, ki = ci & 15;
+    const int sj = cj >> 8, lj = (cj >> 4) & 15, kj = cj & 15;
+    const int ni = 2 * li + 1, nj = 2 * lj + 1;
+    double acc = 0.0;
+    for (int m = 0; m < ni; ++m) {
+        const double ti = sph_coef(li, ki, m);
+        if (ti == 0.0) continue;
+        const double *row = Asph + (size_t)(si + m) * nsph + sj;
+        double r = 0.0;
+        for (int n = 0; n < nj; ++n) r += row[n] * sph_coef(lj, kj, n);
+        acc += ti * r;
+    }
+    Acart[id] = acc;
+}
+
 }  // namespace tg

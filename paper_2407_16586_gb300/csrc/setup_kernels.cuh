@@ -24,5 +24,6 @@ __global__ void k_prim_pairs(int npairs, const int *psa, const int *psb, const i
 __global__ void k_symm(int nbf, const double *A, double *S);
 __global__ void k_fock_combine(int nbf, DensArgs den, double *SJ, double *BK, double *BL);
 __global__ void k_reduce(int n, int nslab, const double *partials, double *grad);
+__global__ void k_sph_to_cart(int nbf, int nsph, const int *cmap, const double *Asph, double *Acart);
 
 }  // namespace tg
