@@ -326,6 +326,14 @@ def run_c3(args, prec, router, torch):
     return 0
 
 
+def shard_full_estimate(step_ms, plan_ms, nshard):
+    """Seconds of a whole gradient from one tile shard's step: the plan
+    (screen and route of every tile of the system) runs once per call
+    whatever the shard, the class kernels of the N shards take N times the
+    shard's (the shards deal every cost-ordered class list round-robin)."""
+    return (plan_ms + nshard * (step_ms - plan_ms)) / 1e3
+
+
 def run_large(args, prec, router, torch):
     """The c4 (300-atom) and c5 (1500-atom) clusters: one step takes many
     minutes (c4) or days (c5, about 4 x 10^11 quartets), so the kernels are
@@ -392,8 +400,8 @@ def run_large(args, prec, router, torch):
                        # the plan (screen and route of ALL tiles) runs once per call, the
                        # class kernels scale with the shard count
                        "full_gradient_s_estimate": {
-                           "mixed": (st["plan_ms"] + nsh * (ms - st["plan_ms"])) / 1e3,
-                           "fp64": (st64["plan_ms"] + nsh * (ms64 - st64["plan_ms"])) / 1e3,
+                           "mixed": shard_full_estimate(ms, st["plan_ms"], nsh),
+                           "fp64": shard_full_estimate(ms64, st64["plan_ms"], nsh),
                            "rule": "plan + N x (step - plan)"},
                        "device_memory_in_use_gb": round((total - free) / 1e9, 2),
                        "host_generate_s": round(t1 - t0, 1), "basis_create_s": round(t2 - t1, 1),

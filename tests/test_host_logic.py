@@ -271,3 +271,12 @@ def test_tile_shards_cover_every_tile_once():
             assert max(counts) - min(counts) <= 1
     with pytest.raises(tg.TGError):
         tg.tg_tile_shard(10, 3, 3)
+
+
+def test_shard_estimate_counts_the_plan_once():
+    """A tile shard's step is its plan (of the whole system) plus 1/N of the
+    class kernels: the whole-gradient estimate adds the plan once."""
+    assert bench.shard_full_estimate(1000.0, 0.0, 32) == pytest.approx(32.0)
+    assert bench.shard_full_estimate(46356.5, 30875.0, 4096) == pytest.approx(30.875 + 4096 * 15.4815)
+    # one shard is the whole gradient
+    assert bench.shard_full_estimate(1234.0, 200.0, 1) == pytest.approx(1.234)
