@@ -1420,10 +1420,12 @@ int tg_grad2e_sph(const tg_basis *cb, int npair, const tg_pair *pairs, const tg_
     tg_options opt;
     if (opt_in) opt = *opt_in;
     else tg_options_default(&opt);
-    if (npair < 1) return TG_EINVAL;
-    if (npair > TG_MAX_PAIRS) return TG_EUNSUPPORTED;
-    for (int p = 0; p < npair; ++p)
-        if (!pairs[p].A || !pairs[p].B) return TG_EINVAL;
+    // every argument is checked before the first CUDA call
+    double om = 0.0;
+    int lr = 0;
+    const int rc0 = check_pairs(npair, pairs, opt, om, lr);
+    if (rc0 != TG_OK) return rc0;
+    if (opt.precision == TG_MIXED_LEARNED && (!opt.router || !opt.router->trained)) return TG_EROUTER;
     cudaStream_t st = (cudaStream_t)opt.stream;
     const size_t nbf = (size_t)b->nbf, nsph = (size_t)b->nsph, natom = (size_t)b->natom;
     const int nup = opt.device_ptrs ? 0 : 2 * npair;

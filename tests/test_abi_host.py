@@ -92,8 +92,11 @@ def test_null_handles_are_rejected(lib):
     opt = tg.tg_options_default()
     arr = (tg.tg_pair * 1)()
     assert lib.tg_grad2e(None, 1, arr, ctypes.byref(opt), g.ctypes.data_as(_dp), ctypes.byref(st)) == tg.TG_EINVAL
+    assert lib.tg_grad2e_sph(None, 1, arr, ctypes.byref(opt), g.ctypes.data_as(_dp),
+                             ctypes.byref(st)) == tg.TG_EINVAL
     assert lib.tg_basis_nbf(None) == tg.TG_EINVAL
     assert lib.tg_basis_natom(None) == tg.TG_EINVAL
+    assert lib.tg_basis_nsph(None) == tg.TG_EINVAL
     lib.tg_basis_destroy(None)  # no-op
     out = ctypes.c_void_p()
     assert lib.tg_batch_create(0, None, None, None, None, ctypes.byref(out)) == tg.TG_EINVAL
