@@ -25,6 +25,10 @@
  *    binomial expansion (x-B_x)^b = sum_k C(b,k) (x-A_x)^k (A_x-B_x)^(b-k).
  *    The erf operator uses [00|00]^(m) = pref * theta^(2m+1) F_m(theta^2 T),
  *    theta^2 = w^2/(w^2+rho); the recursion coefficients are unchanged.
+ *    Every vector of the recursion (P - A, Q - C, P - Q, W - P, W - Q) is
+ *    formed from differences of centres, since the integrals depend on the
+ *    relative positions only; the gradient is then invariant under a rigid
+ *    shift of the molecule to rounding.
  *  - Derivatives (eqs. deriv, deri, eriupdate): d/dA_x of a primitive is
  *    2 zeta (l_x+1 term) - l_x (l_x-1 term).  ALL FOUR centres are
  *    differentiated explicitly; translational invariance is not used, so it
@@ -240,19 +244,31 @@ static void vrr(vrr_ws *w, int Le, int Lf,
                 int bra_on_b, int ket_on_d)
 {
     double p = za + zb, q = zc + zd;
-    double P[3], Q[3], W[3], PA[3], WP[3], QC[3], WQ[3];
+    double PA[3], WP[3], QC[3], WQ[3];
     double ab2 = 0, cd2 = 0, pq2 = 0;
+    /* The integrals depend on relative positions only: P - A = zb/p (B - A),
+       P - B = za/p (A - B), the same for Q, and P - Q = (A - C) + (P - A) -
+       (Q - C), W - P = q/(p+q) (Q - P), W - Q = p/(p+q) (P - Q), all from
+       centre differences (no difference of absolute positions near each
+       other, which would lose digits away from the origin). */
     for (int i = 0; i < 3; ++i) {
-        P[i] = (za * A[i] + zb * B[i]) / p;
-        Q[i] = (zc * C[i] + zd * D[i]) / q;
-        ab2 += (A[i] - B[i]) * (A[i] - B[i]);
-        cd2 += (C[i] - D[i]) * (C[i] - D[i]);
-        pq2 += (P[i] - Q[i]) * (P[i] - Q[i]);
-    }
-    for (int i = 0; i < 3; ++i) {
-        W[i] = (p * P[i] + q * Q[i]) / (p + q);
-        PA[i] = P[i] - (bra_on_b ? B[i] : A[i]); WP[i] = W[i] - P[i];
-        QC[i] = Q[i] - (ket_on_d ? D[i] : C[i]); WQ[i] = W[i] - Q[i];
+        const double ab = A[i] - B[i], cd = C[i] - D[i];
+        ab2 += ab * ab;
+        cd2 += cd * cd;
+#if OR_MUTATION == 16
+        /* product centres as absolute positions, differences taken afterwards */
+        const double Pi = (za * A[i] + zb * B[i]) / p, Qi = (zc * C[i] + zd * D[i]) / q;
+        const double pa = Pi - A[i], pb = Pi - B[i], qc = Qi - C[i], qd = Qi - D[i];
+        const double pq = Pi - Qi;
+#else
+        const double pa = -zb / p * ab, pb = za / p * ab, qc = -zd / q * cd, qd = zc / q * cd;
+        const double pq = (A[i] - C[i]) + pa - qc;
+#endif
+        pq2 += pq * pq;
+        PA[i] = bra_on_b ? pb : pa;
+        QC[i] = ket_on_d ? qd : qc;
+        WP[i] = -q / (p + q) * pq;
+        WQ[i] = p / (p + q) * pq;
     }
     double rho = p * q / (p + q);
     double T = rho * pq2;

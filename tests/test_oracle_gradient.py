@@ -227,3 +227,15 @@ def test_class_filter_partitions_the_quartets(c1):
         n += nqq
     assert n == nq
     assert np.abs(tot - g).max() <= 1e-12 * max(1.0, np.abs(g).max())
+
+
+def test_rigid_translation_leaves_the_gradient_unchanged():
+    """The integrals, and so the gradient, depend on the relative positions of
+    the centres only (Sec. II.C): shifting the whole molecule by tens of bohr
+    changes the c1 gradient by rounding only (the oracle forms P - A, P - Q
+    and W - P from centre differences)."""
+    s = synth.config(0)
+    g0 = oracle.grad2e(s, tau=0.0)[0]
+    for shift in ([40.0, 35.0, -30.0], [-120.0, 5.0, 60.0]):
+        g1 = oracle.grad2e(s, tau=0.0, xyz=s["xyz"] + np.array(shift))[0]
+        assert np.abs(g1 - g0).max() <= 1e-12 * np.abs(g0).max(), shift

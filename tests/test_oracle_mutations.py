@@ -47,6 +47,7 @@ MUTATIONS = {
     13: ("coefficient of shell d taken at shell c's primitive index", "contraction"),
     14: ("first primitive's coefficient of shell b used for all its primitives", "contraction"),
     15: ("Fock exchange block read with the density transposed", "fock"),
+    16: ("product centres kept as absolute positions (P - A by cancellation)", "translation"),
 }
 
 
@@ -209,7 +210,16 @@ def pin_fock():
     return abs(float(np.sum(A * F)) - e) <= 1e-12 * abs(e)
 
 
-PINS = {"gamma": pin_gamma, "contraction": pin_contraction, "fock": pin_fock, "boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
+def pin_translation():
+    """The integrals depend on relative positions only: a rigid shift of
+    every centre by tens of bohr leaves the c1 gradient unchanged."""
+    s = synth.config(0)
+    g0 = oracle.grad2e(s, tau=0.0)[0]
+    g1 = oracle.grad2e(s, tau=0.0, xyz=s["xyz"] + np.array([40.0, 35.0, -30.0]))[0]
+    return float(np.abs(g1 - g0).max()) <= 1e-12 * float(np.abs(g0).max())
+
+
+PINS = {"translation": pin_translation, "gamma": pin_gamma, "contraction": pin_contraction, "fock": pin_fock, "boys": pin_boys, "norm": pin_norm, "ssss": pin_ssss, "quadrature": pin_quadrature, "fd": pin_fd,
         "canonical": pin_canonical}
 
 
